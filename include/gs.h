@@ -1,0 +1,218 @@
+/*
+ * gs.h — C ABI of the B300 (sm_103a) tile-based Gaussian splatting renderer
+ * with the exponential kernel and the polynomial-plus-ReLU kernels of
+ * "From ex(p) to poly: Gaussian Splatting with Polynomial Kernels"
+ * (Mueller, Winter, Steinberger; arXiv 2603.18707).
+ *
+ * Pipeline (one stream, all stream-ordered):
+ *   gs_preprocess       project splats into every camera, per-splat support
+ *                       threshold and tile rectangle (Eq. 1, Eq. 3-6, Sec. 3.4, App. B)
+ *   gs_bin_sort         depth order + tile binning: compaction, radix sorts,
+ *                       overlap emission, per-tile ranges
+ *   gs_render           front-to-back alpha blending per tile (Sec. 2, Eq. 1/2/6)
+ *   gs_render_backward  reverse blend + chain rule to the splat inputs (Sec. 4.3)
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named d_* are DEVICE pointers; everything else is host memory.
+ *  - The caller allocates every buffer; no entry point allocates or frees
+ *    device or host memory. Workspace sizes come from the *_bytes queries.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued asynchronously; host-side arguments (cameras, config)
+ *    are copied into kernel parameters before the call returns.
+ *  - Errors: every call returns gs_status. Argument errors are detected on
+ *    the host before anything is launched. Conditions only the device can see
+ *    (overlap capacity exceeded, a bounded spin-wait that timed out) are OR-ed
+ *    into an error word inside the bin/sort workspace; read it with
+ *    gs_workspace_status. No entry point exits, traps or prints.
+ *  - Floating point: every device computation is FP32 (FP16x2 where the config
+ *    asks for it); no FP64 on the device.
+ *  - Splat inputs are the activated values the paper's Sec. 2 names: means mu
+ *    [P][3]; scales s [P][3] (> 0); rotation quaternions q [P][4] in
+ *    (w, x, y, z) order (any non-zero norm: they are normalised internally);
+ *    opacities o [P] in [0, 1]; SH coefficients [P][(d+1)^2][3], degree d <= 3.
+ *    All row-major FP32.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GS_ABI_VERSION 1
+#define GS_MAX_CAMERAS 64
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_ARG = 1,         /* invalid argument (host check, nothing launched) */
+    GS_ERR_CUDA = 2,        /* a CUDA launch or copy failed */
+    GS_ERR_CAPACITY = 4,    /* device: more tile overlaps than the given capacity */
+    GS_ERR_TIMEOUT = 8,     /* device: a bounded spin-wait gave up */
+    GS_ERR_UNSUPPORTED = 16 /* valid but not implemented for this config */
+} gs_status;
+
+/* Kernel k(x) on the quadric x = Q(v) (Sec. 3):
+ *   GS_K_EXP   g(x) = exp(-x/2)                                  (Eq. 1)
+ *   GS_K_POLY1 f1(x) = max(c0 + c1 x, 0)                         (Eq. 2)
+ *   GS_K_POLY2 f'2(x) = c0 + c1 x + c2 x^2 if x < x0, else 0     (Eq. 6)
+ *   GS_K_POLY3 f3(x) = max(c0 + c1 x + c2 x^2 + c3 x^3, 0)      (Eq. 2)
+ * x0 is the first positive root of the polynomial. */
+typedef enum { GS_K_EXP = 0, GS_K_POLY1 = 1, GS_K_POLY2 = 2, GS_K_POLY3 = 3 } gs_kernel_kind;
+
+/* Support threshold (culling radius), in quadric units:
+ *   GS_CULL_UNIVERSAL opacity-free: poly x0 (Eq. 5, App. B with eps = 0);
+ *                     exp -2 ln(eps) (3.3 sigma, Sec. 3.1)
+ *   GS_CULL_OPACITY   per splat: exp 2 ln(o'/eps) (Eq. 3); f1 (eps - o' c0)/(o' c1)
+ *                     (Eq. 4); f'2/f3 first root of poly = eps/o' (App. B);
+ *                     splats with o' k(0) < eps are dropped
+ *   GS_CULL_LEGACY3   3 sigma (x = 9) of the original 3DGS (Sec. 2.1); not
+ *                     pixel-exact for exp */
+typedef enum { GS_CULL_UNIVERSAL = 0, GS_CULL_OPACITY = 1, GS_CULL_LEGACY3 = 2 } gs_cull;
+
+/* Screen rectangle around the support ellipse {d : d^T conic d <= x_cut}:
+ * its exact axis-aligned bounding box, or the 3DGS square around the circle
+ * of radius sqrt(x_cut * lambda_max). Both are conservative. */
+typedef enum { GS_RECT_AABB = 0, GS_RECT_CIRCLE = 1 } gs_rect_mode;
+
+/* Pinhole camera. viewmat: world -> camera, row-major 4x4; camera looks
+ * along +z with +x right and +y down. A world point p maps to
+ * t = R p + T and to pixel coordinates (fx tx/tz + cx, fy ty/tz + cy);
+ * pixel (i, j) has its centre at (i + 0.5, j + 0.5). Splats with
+ * tz <= znear are dropped. */
+typedef struct {
+    float viewmat[16];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float znear;
+    int32_t reserved;
+} gs_camera;
+
+typedef struct {
+    int32_t kind;         /* gs_kernel_kind */
+    float c[4];           /* polynomial coefficients c0..c3 (unused ones 0) */
+    int32_t cull;         /* gs_cull */
+    float eps;            /* alpha threshold, 1/255 (Sec. 3.1) */
+    float alpha_max;      /* alpha clamp, 0.99 (3DGS) */
+    float t_min;          /* transmittance stop, 1e-4 (3DGS) */
+    int32_t aa_normalize; /* 1: o' = o sqrt(|Sigma'| / |Sigma' + v I|) (Sec. 3.4) */
+    float aa_dilation;    /* v added to the 2D covariance diagonal, 0.3 */
+    int32_t tile_w;       /* tile width in pixels: 8, 16 or 32 */
+    int32_t tile_h;       /* tile height in pixels: 8 or 16 */
+    int32_t rect_mode;    /* gs_rect_mode */
+    int32_t batch;        /* splats staged in shared memory per round: 32..256 */
+    int32_t px_per_thread;/* pixels per thread in the blend: 1, 2 or 4 */
+    int32_t fp16x2;       /* 1: quadric and polynomial in packed FP16x2 */
+    int32_t reserved[4];
+} gs_config;
+
+/* Fills a config with the defaults above for a kernel kind. f1 uses the
+ * paper's coefficients (Sec. 3.1, with the printed c0/c1 labels swapped:
+ * c0 = 0.773, c1 = -0.773/4.386, root 4.386); f'2 and f3 use this library's
+ * L1 fits by the Sec. 3.1 procedure (the paper does not print them). */
+gs_status gs_config_default(int32_t kind, int32_t cull, gs_config *cfg);
+
+/* Byte size of the per-(camera, splat) record buffer that gs_preprocess
+ * writes and the later stages read, for ncam * P records. Layout, with
+ * N = ncam * P and records camera-major (index c * P + i):
+ *   float4 rec[N][3]   (mean.x, mean.y, o', depth), (A, B, C, x_cut),
+ *                      (red, green, blue, rho) with conic (A, B, C) = (Sigma'+vI)^-1
+ *                      and rho the AA factor
+ *   uint16 rect[N][4]  tile x0, y0, x1, y1 (inclusive) of the support rectangle
+ *   uint32 tiles[N]    number of tiles in rect; 0 = splat not drawn
+ *   uint32 dkey[N]     float bits of depth (drawn splats only)
+ * each array 256-byte aligned. */
+size_t gs_splat2d_bytes(int32_t ncam, int32_t P);
+
+/* Projection of P splats into ncam cameras (ncam <= GS_MAX_CAMERAS): EWA
+ * covariance Sigma' = J W Sigma W^T J^T + v I (Eq. 1; 3DGS), the AA factor of
+ * Sec. 3.4, conic, depth, SH colour (3DGS real SH + 0.5, clamped at 0),
+ * support threshold x_cut (Eq. 3-5, App. B) and tile rectangle.
+ * d_splat2d: gs_splat2d_bytes(ncam, P) bytes of device memory. */
+gs_status gs_preprocess(void *stream, const gs_camera *cams, int32_t ncam, int32_t P,
+                        const float *d_means, const float *d_scales, const float *d_quats,
+                        const float *d_opacities, const float *d_sh, int32_t sh_degree,
+                        const gs_config *cfg, void *d_splat2d);
+
+/* Total tile count over all cameras; the global tile id of camera c's tile
+ * (tx, ty) is base_c + ty * ceil(W_c / tile_w) + tx, cameras in order. */
+int64_t gs_total_tiles(const gs_camera *cams, int32_t ncam, const gs_config *cfg);
+
+/* Workspace bytes for gs_bin_sort with N = ncam * P records, room for
+ * `capacity` splat-tile overlaps and `total_tiles` tiles. */
+size_t gs_bin_sort_workspace_bytes(int64_t n_records, int64_t capacity, int64_t total_tiles);
+
+/* Depth-ordered tile binning of the records written by gs_preprocess.
+ * Result: for global tile t, d_vals[d_ranges[2t] .. d_ranges[2t+1]) are the
+ * record indices (c * P + i) of the splats whose rectangle contains t, in
+ * increasing (depth, i) order — a stable sort of the 64-bit keys
+ * (tile << 32 | depth bits) 3DGS uses. Implemented as a stable LSD radix sort
+ * of the drawn records by depth followed by a stable LSD radix sort of the
+ * emitted overlaps by tile id, both Onesweep (one pass per 8-bit digit,
+ * decoupled look-back with a bounded wait).
+ *   d_vals:      uint32 [capacity]
+ *   d_ranges:    uint32 [2 * total_tiles] (start, end) per tile
+ *   d_keys64:    optional uint64 [capacity] (may be NULL): the sorted keys
+ *   d_count:     optional uint32 [3] (may be NULL): drawn records, overlaps
+ *                stored, overlaps counted (the capacity needed)
+ * Overlaps beyond `capacity` are dropped and GS_ERR_CAPACITY is raised in the
+ * workspace error word. At most 2^30 - 1 records and overlaps per call. */
+gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t ncam, int32_t P,
+                      const gs_config *cfg, const void *d_splat2d, int64_t capacity,
+                      void *d_workspace, size_t workspace_bytes, uint32_t *d_vals,
+                      uint32_t *d_ranges, uint64_t *d_keys64, uint32_t *d_count);
+
+/* Front-to-back blending per tile (Sec. 2): for each pixel, over its tile's
+ * list in order, alpha = min(alpha_max, o' k(Q)) with Q the quadric at the
+ * pixel centre; entries with alpha < eps are skipped; the walk stops at the
+ * first entry whose T (1 - alpha) would drop below t_min, without adding it;
+ * out = sum c alpha T + T bg.
+ *   d_out_rgb:   float [sum_c H_c W_c][3], cameras back to back, row-major
+ *   d_final_T:   float [sum_c H_c W_c] (may be NULL)
+ *   d_last:      uint32 [sum_c H_c W_c] 1 + list position of the last
+ *                contributing entry, 0 if none (may be NULL; the backward
+ *                pass needs it)
+ *   d_n_eval:    uint32 [sum_c H_c W_c] list entries evaluated (may be NULL)
+ *   bg:          host float[3] background colour */
+gs_status gs_render(void *stream, const gs_camera *cams, int32_t ncam, int32_t P,
+                    const gs_config *cfg, const void *d_splat2d, const uint32_t *d_vals,
+                    const uint32_t *d_ranges, const float *bg, float *d_out_rgb,
+                    float *d_final_T, uint32_t *d_last, uint32_t *d_n_eval);
+
+/* Reverse pass of gs_render and gs_preprocess for one or more cameras:
+ * gradients of a loss L with respect to the splat inputs, given
+ * dL/d(out_rgb). Needs the forward's d_final_T and d_last. Output gradient
+ * buffers are ACCUMULATED into (the caller zeroes them): d_grad_means [P][3],
+ * d_grad_scales [P][3], d_grad_quats [P][4] (for the quaternion as given,
+ * before normalisation), d_grad_opacities [P], d_grad_sh [P][(d+1)^2][3].
+ * d_grad2d: scratch of gs_grad2d_bytes(ncam, P) bytes (zeroed by the call). */
+size_t gs_grad2d_bytes(int32_t ncam, int32_t P);
+gs_status gs_render_backward(void *stream, const gs_camera *cams, int32_t ncam, int32_t P,
+                             const gs_config *cfg, const float *d_means,
+                             const float *d_scales, const float *d_quats,
+                             const float *d_opacities, const float *d_sh, int32_t sh_degree,
+                             const void *d_splat2d, const uint32_t *d_vals,
+                             const uint32_t *d_ranges, const float *bg,
+                             const float *d_final_T, const uint32_t *d_last,
+                             const float *d_grad_out, void *d_grad2d,
+                             float *d_grad_means, float *d_grad_scales, float *d_grad_quats,
+                             float *d_grad_opacities, float *d_grad_sh);
+
+/* Reads (synchronously, on `stream`) the device error word of a bin/sort
+ * workspace into *code (OR of GS_ERR_CAPACITY / GS_ERR_TIMEOUT) and clears
+ * it. Returns GS_ERR_CUDA if the copy fails. */
+gs_status gs_workspace_status(void *stream, void *d_workspace, int32_t *code);
+
+/* Number of kernels this library has launched in this process (all entry
+ * points), for launch accounting. */
+uint64_t gs_launch_count(void);
+
+/* Human-readable name of a status bit. */
+const char *gs_status_string(int32_t status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H */

@@ -96,7 +96,7 @@ def lib():
                                          _DP, _DP, _DP, _I64P]
         L.orc_render_untiled.restype = None
         L.orc_render_tiled.argtypes = [C.c_int, C.c_void_p, C.POINTER(Camera), C.POINTER(Config),
-                                       _DP, C.c_int, _I32P, _DP, _DP, _I64P, _I64P, _I64P]
+                                       _DP, C.c_int, _I32P, _DP, _DP, _I64P, _I64P, _I64P, _DP]
         L.orc_render_tiled.restype = None
         L.orc_render_backward.argtypes = [C.c_int, _DP, _DP, _DP, _DP, _DP, C.c_int,
                                           C.POINTER(Camera), C.POINTER(Config), _DP, _DP,
@@ -255,10 +255,12 @@ def render_untiled(sc: dict, cam: Camera, cfg: Config, bg=(0.0, 0.0, 0.0), s2d=N
     return img, T, nc
 
 
-def render_tiled(sc: dict, cam: Camera, cfg: Config, bg=(0.0, 0.0, 0.0), tiles=None, s2d=None):
+def render_tiled(sc: dict, cam: Camera, cfg: Config, bg=(0.0, 0.0, 0.0), tiles=None, s2d=None,
+                 with_margin: bool = False):
     """Tile-binned render; ``tiles``: iterable of tile ids (default all).
     Returns image, final T, last contributor, evaluations per pixel, list
-    length per tile."""
+    length per tile (and, with ``with_margin``, the per-pixel decision
+    margin: relative distance of the closest skip / stop decision)."""
     if s2d is None:
         s2d = project(sc, cam, cfg)
     P = np.asarray(sc["means"]).size // 3
@@ -270,6 +272,7 @@ def render_tiled(sc: dict, cam: Camera, cfg: Config, bg=(0.0, 0.0, 0.0), tiles=N
     last = np.zeros((H, W), dtype=np.int64)
     nev = np.zeros((H, W), dtype=np.int64)
     llen = np.zeros(tx * ty, dtype=np.int64)
+    margin = np.full((H, W), np.inf)
     if tiles is None:
         sel = np.zeros(1, dtype=np.int32)
         nsel = -1
@@ -280,7 +283,9 @@ def render_tiled(sc: dict, cam: Camera, cfg: Config, bg=(0.0, 0.0, 0.0), tiles=N
             sel = np.zeros(1, dtype=np.int32)
     lib().orc_render_tiled(P, C.addressof(s2d), C.byref(cam), C.byref(cfg),
                            np.asarray(bg, dtype=np.float64), nsel, sel, img.reshape(-1),
-                           T.reshape(-1), last.reshape(-1), nev.reshape(-1), llen)
+                           T.reshape(-1), last.reshape(-1), nev.reshape(-1), llen, margin.reshape(-1))
+    if with_margin:
+        return img, T, last, nev, llen, margin
     return img, T, last, nev, llen
 
 

@@ -497,18 +497,25 @@ static double quadric(const orc_splat2d *s, double px, double py)
  */
 static long long composite_pixel(const orc_splat2d *s, const int *order, long long n,
                                  const orc_config *cfg, double x0, double px, double py,
-                                 const double bg[3], double out[3], double *Tout, long long *last)
+                                 const double bg[3], double out[3], double *Tout, long long *last,
+                                 double *margin)
 {
     double T = 1.0, C[3] = {0.0, 0.0, 0.0};
     long long evaluated = n;
+    double m = INFINITY;
     *last = 0;
     for (long long j = 0; j < n; ++j) {
         const orc_splat2d *g = &s[order[j]];
         double Q = quadric(g, px, py);
         double alpha = g->opacity * orc_kernel(cfg, x0, Q);
+        /* diagnostic only: relative distance of this entry's skip decision */
+        double me = fabs(alpha - cfg->eps) / cfg->eps;
+        if (me < m) m = me;
         if (alpha > cfg->alpha_max) alpha = cfg->alpha_max;
         if (alpha < cfg->eps) continue;
         double Tn = T * (1.0 - alpha);
+        double ms = fabs(Tn - cfg->t_min) / cfg->t_min;
+        if (ms < m) m = ms;
         if (Tn < cfg->t_min) {
             evaluated = j + 1;
             break;
@@ -519,6 +526,7 @@ static long long composite_pixel(const orc_splat2d *s, const int *order, long lo
     }
     for (int ch = 0; ch < 3; ++ch) out[ch] = C[ch] + T * bg[ch];
     *Tout = T;
+    if (margin) *margin = m;
     return evaluated;
 }
 
@@ -536,7 +544,7 @@ void orc_render_untiled(int P, const orc_splat2d *s, const orc_camera *cam,
         for (int x = 0; x < W; ++x) {
             long long p = (long long)y * W + x, last;
             double T;
-            composite_pixel(s, order, n, cfg, x0, x + 0.5, y + 0.5, bg, img + 3 * p, &T, &last);
+            composite_pixel(s, order, n, cfg, x0, x + 0.5, y + 0.5, bg, img + 3 * p, &T, &last, NULL);
             if (final_T) final_T[p] = T;
             if (n_contrib) n_contrib[p] = last;
         }
@@ -548,13 +556,16 @@ void orc_render_untiled(int P, const orc_splat2d *s, const orc_camera *cam,
  * contains it, in (depth, index) order. With a conservative x_cut this equals
  * the untiled render exactly. tiles_sel lists the tile ids to render
  * (n_tiles_sel < 0: all tiles); pixels of other tiles are left untouched.
- * n_eval: entries evaluated per pixel; list_len: list length per tile.
+ * n_eval: entries evaluated per pixel; list_len: list length per tile;
+ * margin (optional, diagnostic): per pixel, the smallest relative distance of
+ * any skip (alpha vs eps) or stop (T (1 - alpha) vs t_min) decision from its
+ * threshold — pixels where a lower-precision renderer may decide otherwise.
  */
 void orc_render_tiled(int P, const orc_splat2d *s, const orc_camera *cam,
                       const orc_config *cfg, const double bg[3],
                       int n_tiles_sel, const int *tiles_sel,
                       double *img, double *final_T, long long *last_contrib,
-                      long long *n_eval, long long *list_len)
+                      long long *n_eval, long long *list_len, double *margin)
 {
     int n;
     int *order = sorted_visible(P, s, &n);
@@ -578,7 +589,8 @@ void orc_render_tiled(int P, const orc_splat2d *s, const orc_camera *cam,
             for (int x = gx * cfg->tile_w; x < (gx + 1) * cfg->tile_w && x < W; ++x) {
                 long long p = (long long)y * W + x, last;
                 double T;
-                long long ev = composite_pixel(s, list, m, cfg, x0, x + 0.5, y + 0.5, bg, img + 3 * p, &T, &last);
+                long long ev = composite_pixel(s, list, m, cfg, x0, x + 0.5, y + 0.5, bg, img + 3 * p, &T,
+                                               &last, margin ? margin + p : NULL);
                 if (final_T) final_T[p] = T;
                 if (last_contrib) last_contrib[p] = last;
                 if (n_eval) n_eval[p] = ev;

@@ -94,7 +94,7 @@ void orc_render_tiled(int P, const orc_splat2d *s, const orc_camera *cam,
                       const orc_config *cfg, const double bg[3],
                       int n_tiles_sel, const int *tiles_sel,
                       double *img, double *final_T, long long *last_contrib,
-                      long long *n_eval, long long *list_len);
+                      long long *n_eval, long long *list_len, double *margin);
 
 /* ---- analytic reverse pass (Sec. 4.3 ablation "Opt" rows need it) ---- */
 void orc_render_backward(int P, const double *means, const double *scales,

@@ -1,0 +1,148 @@
+"""Python binding of the C ABI with the same entry-point names.
+
+Marshalling only: torch tensors are passed as device pointers, the current
+torch CUDA stream is passed as the stream, cameras and configs as ctypes
+structs. Nothing here computes any part of the rendering path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import GsCamera, GsConfig, check, lib
+
+
+def make_camera(d: dict) -> GsCamera:
+    """ctypes camera from a dict with viewmat (4x4 world->camera, row-major),
+    fx, fy, cx, cy, width, height and optional znear."""
+    c = GsCamera()
+    vm = np.asarray(d["viewmat"], dtype=np.float64).reshape(16)
+    for i in range(16):
+        c.viewmat[i] = float(vm[i])
+    c.fx, c.fy, c.cx, c.cy = float(d["fx"]), float(d["fy"]), float(d["cx"]), float(d["cy"])
+    c.width, c.height = int(d["width"]), int(d["height"])
+    c.znear = float(d.get("znear", 0.2))
+    return c
+
+
+def camera_array(cams) -> C.Array:
+    cams = list(cams)
+    if not 1 <= len(cams) <= _lib.GS_MAX_CAMERAS:
+        raise ValueError(f"1..{_lib.GS_MAX_CAMERAS} cameras per call")
+    arr = (GsCamera * len(cams))()
+    for i, d in enumerate(cams):
+        arr[i] = d if isinstance(d, GsCamera) else make_camera(d)
+    return arr
+
+
+def make_config(kind="poly1", cull="opacity", **over) -> GsConfig:
+    """Library defaults for a kernel kind and cull mode (gs_config_default),
+    then field overrides, e.g. tile=(8, 8), coeffs=(...), aa=False."""
+    cfg = GsConfig()
+    k = _lib.KIND[kind] if isinstance(kind, str) else int(kind)
+    cu = _lib.CULL[cull] if isinstance(cull, str) else int(cull)
+    check("gs_config_default", lib().gs_config_default(k, cu, C.byref(cfg)))
+    for key, val in over.items():
+        if key == "tile":
+            cfg.tile_w, cfg.tile_h = int(val[0]), int(val[1])
+        elif key == "coeffs":
+            vals = list(val) + [0.0] * (4 - len(val))
+            for i in range(4):
+                cfg.c[i] = float(vals[i])
+        elif key == "aa":
+            cfg.aa_normalize = int(bool(val))
+        elif key == "rect":
+            cfg.rect_mode = {"aabb": _lib.GS_RECT_AABB, "circle": _lib.GS_RECT_CIRCLE}[val]
+        else:
+            setattr(cfg, key, val)
+    return cfg
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _p(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    if not t.is_contiguous():
+        raise ValueError("contiguous tensor expected")
+    return t.data_ptr()
+
+
+def _f32(t):
+    if t is not None and t.dtype != torch.float32:
+        raise ValueError("float32 tensor expected")
+    return _p(t)
+
+
+def gs_splat2d_bytes(ncam: int, P: int) -> int:
+    return int(lib().gs_splat2d_bytes(ncam, P))
+
+
+def gs_total_tiles(cams, cfg: GsConfig) -> int:
+    arr = camera_array(cams)
+    return int(lib().gs_total_tiles(arr, len(arr), C.byref(cfg)))
+
+
+def gs_bin_sort_workspace_bytes(n_records: int, capacity: int, total_tiles: int) -> int:
+    return int(lib().gs_bin_sort_workspace_bytes(n_records, capacity, total_tiles))
+
+
+def gs_grad2d_bytes(ncam: int, P: int) -> int:
+    return int(lib().gs_grad2d_bytes(ncam, P))
+
+
+def gs_preprocess(cams, P, means, scales, quats, opacities, sh, sh_degree, cfg, splat2d, stream=None):
+    arr = camera_array(cams)
+    check("gs_preprocess", lib().gs_preprocess(
+        _stream(stream), arr, len(arr), int(P), _f32(means), _f32(scales), _f32(quats),
+        _f32(opacities), _f32(sh), int(sh_degree), C.byref(cfg), _p(splat2d)))
+
+
+def gs_bin_sort(cams, P, cfg, splat2d, capacity, workspace, vals, ranges, keys64=None, count=None,
+                stream=None):
+    arr = camera_array(cams)
+    check("gs_bin_sort", lib().gs_bin_sort(
+        _stream(stream), arr, len(arr), int(P), C.byref(cfg), _p(splat2d), int(capacity),
+        _p(workspace), workspace.numel() * workspace.element_size(), _p(vals), _p(ranges),
+        _p(keys64), _p(count)))
+
+
+def gs_render(cams, P, cfg, splat2d, vals, ranges, bg, out_rgb, final_T=None, last=None,
+              n_eval=None, stream=None):
+    arr = camera_array(cams)
+    bgc = (C.c_float * 3)(*[float(v) for v in bg])
+    check("gs_render", lib().gs_render(
+        _stream(stream), arr, len(arr), int(P), C.byref(cfg), _p(splat2d), _p(vals), _p(ranges),
+        bgc, _f32(out_rgb), _f32(final_T), _p(last), _p(n_eval)))
+
+
+def gs_render_backward(cams, P, cfg, means, scales, quats, opacities, sh, sh_degree, splat2d, vals,
+                       ranges, bg, final_T, last, grad_out, grad2d, grad_means, grad_scales,
+                       grad_quats, grad_opacities, grad_sh, stream=None):
+    arr = camera_array(cams)
+    bgc = (C.c_float * 3)(*[float(v) for v in bg])
+    check("gs_render_backward", lib().gs_render_backward(
+        _stream(stream), arr, len(arr), int(P), C.byref(cfg), _f32(means), _f32(scales),
+        _f32(quats), _f32(opacities), _f32(sh), int(sh_degree), _p(splat2d), _p(vals),
+        _p(ranges), bgc, _f32(final_T), _p(last), _f32(grad_out), _p(grad2d), _f32(grad_means),
+        _f32(grad_scales), _f32(grad_quats), _f32(grad_opacities), _f32(grad_sh)))
+
+
+def gs_workspace_status(workspace, stream=None) -> int:
+    code = C.c_int32(0)
+    check("gs_workspace_status", lib().gs_workspace_status(_stream(stream), _p(workspace),
+                                                           C.byref(code)))
+    return int(code.value)
+
+
+def gs_launch_count() -> int:
+    return int(lib().gs_launch_count())

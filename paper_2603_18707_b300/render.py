@@ -1,0 +1,113 @@
+"""Frame-level driver: owns the device buffers of one camera set and runs
+preprocess -> bin/sort -> blend on the current CUDA stream.
+
+Buffer management only (torch allocates, the library computes). The overlap
+capacity is sized on first use: a run whose overlap count exceeds the
+capacity is detected from the device counters and repeated with a larger
+buffer (outside any timed or captured region).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import api
+from ._lib import GS_ERR_CAPACITY
+
+
+def activate(scene: dict, device="cuda") -> dict:
+    """3DGS activations of raw parameters: scale = exp(log-scale), opacity =
+    sigmoid(logit). Means, quaternions (normalised inside the library) and SH
+    are passed through."""
+    t = lambda a: torch.as_tensor(a, dtype=torch.float32, device=device).contiguous()
+    return {"means": t(scene["means"]), "scales": torch.exp(t(scene["log_scales"])),
+            "quats": t(scene["quats"]), "opacities": torch.sigmoid(t(scene["opacity_logits"])),
+            "sh": t(scene["sh"]), "sh_degree": int(scene["sh_degree"])}
+
+
+class Rasterizer:
+    """Renders P splats into a fixed list of cameras (at most 64)."""
+
+    def __init__(self, cams, cfg, P: int, capacity: int | None = None, device="cuda",
+                 keep_keys: bool = False):
+        self.cams = api.camera_array(cams)
+        self.ncam = len(self.cams)
+        self.cfg = cfg
+        self.P = int(P)
+        self.device = torch.device(device)
+        self.total_tiles = api.gs_total_tiles(self.cams, cfg)
+        self.sizes = [(c.height, c.width) for c in self.cams]
+        self.npix = sum(h * w for h, w in self.sizes)
+        u8 = dict(dtype=torch.uint8, device=self.device)
+        i32 = dict(dtype=torch.int32, device=self.device)
+        self.splat2d = torch.empty(api.gs_splat2d_bytes(self.ncam, self.P), **u8)
+        self.ranges = torch.zeros(2 * self.total_tiles, **i32)
+        self.count = torch.zeros(3, **i32)
+        self.out = torch.empty(self.npix, 3, dtype=torch.float32, device=self.device)
+        self.final_T = torch.empty(self.npix, dtype=torch.float32, device=self.device)
+        self.last = torch.empty(self.npix, **i32)
+        self.n_eval = torch.empty(self.npix, **i32)
+        self.keep_keys = keep_keys
+        self.capacity = 0
+        self._alloc(capacity if capacity else max(1 << 20, 8 * self.ncam * self.P))
+
+    def _alloc(self, capacity: int):
+        self.capacity = int(capacity)
+        n_rec = self.ncam * self.P
+        ws = api.gs_bin_sort_workspace_bytes(n_rec, self.capacity, self.total_tiles)
+        self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
+        self.vals = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=self.device)
+        self.keys64 = (torch.empty(max(self.capacity, 1), dtype=torch.int64, device=self.device)
+                       if self.keep_keys else None)
+
+    def preprocess(self, sc: dict):
+        api.gs_preprocess(self.cams, self.P, sc["means"], sc["scales"], sc["quats"],
+                          sc["opacities"], sc["sh"], sc["sh_degree"], self.cfg, self.splat2d)
+
+    def bin_sort(self):
+        api.gs_bin_sort(self.cams, self.P, self.cfg, self.splat2d, self.capacity, self.workspace,
+                        self.vals, self.ranges, self.keys64, self.count)
+
+    def blend(self, bg=(0.0, 0.0, 0.0), n_eval: bool = True):
+        api.gs_render(self.cams, self.P, self.cfg, self.splat2d, self.vals, self.ranges, bg,
+                      self.out, self.final_T, self.last, self.n_eval if n_eval else None)
+
+    def forward(self, sc: dict, bg=(0.0, 0.0, 0.0), n_eval: bool = True):
+        """One pass of the whole path; grows the overlap buffer if needed."""
+        for _ in range(3):
+            self.preprocess(sc)
+            self.bin_sort()
+            self.blend(bg, n_eval)
+            err = api.gs_workspace_status(self.workspace)
+            if not err & GS_ERR_CAPACITY:
+                if err:
+                    raise RuntimeError(f"device error word {err}")
+                return self.out
+            need = int(self.count[2].item() & 0xFFFFFFFF)
+            self._alloc(int(max(need, self.capacity) * 1.25) + 1024)
+        raise RuntimeError("overlap capacity could not be sized")
+
+    def run_async(self, sc: dict, bg=(0.0, 0.0, 0.0), n_eval: bool = False):
+        """The same pass without any host synchronisation (for timing and
+        graph capture, after forward() has sized the buffers)."""
+        self.preprocess(sc)
+        self.bin_sort()
+        self.blend(bg, n_eval)
+        return self.out
+
+    def images(self):
+        out, o = [], 0
+        for h, w in self.sizes:
+            out.append(self.out[o:o + h * w].view(h, w, 3))
+            o += h * w
+        return out
+
+    def per_camera(self, t):
+        out, o = [], 0
+        for h, w in self.sizes:
+            out.append(t[o:o + h * w].view(h, w))
+            o += h * w
+        return out
+
+    def n_records(self) -> tuple[int, int]:
+        c = self.count.cpu().tolist()
+        return c[0] & 0xFFFFFFFF, c[1] & 0xFFFFFFFF
