@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Throughput of the polynomial-kernel splatting path on B300.
+
+Workload: a 3M-splat cluster-mixture scene (SH degree 3) rendered at
+1920x1080 into 16 cameras on an orbit. One step = one pass of the whole
+path (projection, binning, blending) for all 16 cameras. The headline arm is
+the first-order polynomial kernel with opacity-dependent culling; the
+exponential kernel with its opacity-dependent radius runs beside it on the
+same scene and cameras.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun every rank renders its own
+copy of the workload (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s and Gsplat-evals/s, poly-1+opacity-cull vs exp on same B300 at ≥45 dB vs exp"
+# FP32 FLOPs of one splat evaluation (FMA = 2): dx, dy (2); Q = A dx^2 +
+# 2 B dx dy + C dy^2 (7); kernel and opacity: f1 c0 + c1 Q and o' * (3),
+# exp -Q/2 and o' * (2, plus one MUFU ex2); blend T (1 - a), a T,
+# C += c a T (9).
+FLOP_PER_EVAL = {"poly1": 21, "exp": 20}
+SMS, FP32_LANES = 148, 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=60)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--splats", type=int, default=3_000_000)
+    p.add_argument("--cams", type=int, default=16)
+    p.add_argument("--width", type=int, default=1920)
+    p.add_argument("--height", type=int, default=1080)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def workload(a):
+    return {"workload": f"{a.splats // 1_000_000}M-splat cluster scene, SH degree 3, "
+                        f"{a.cams} orbit cameras at {a.width}x{a.height}",
+            "splats": a.splats, "cameras": a.cams, "resolution": f"{a.width}x{a.height}",
+            "sh_degree": 3, "tile": "16x16", "kernel": "poly1", "cull": "opacity",
+            "baseline_kernel": "exp", "baseline_cull": "opacity",
+            "l2": "inputs larger than L2 (scene 0.7 GB, records 3 GB per step)"}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu, self.lines, self.proc = gpu, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 6:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(a):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if a.impl == "ours" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(raw, cam, n_tiles: int, seed: int = 0):
+    """Times the FP64 oracle on one camera: projection of every splat plus
+    the tile-binned render of n_tiles tiles. Returns (frame seconds
+    extrapolated to all tiles, sample seconds, description)."""
+    import numpy as np
+    import oracle
+    oc = oracle.camera_from_dict(cam)
+    co = json.load(open(os.path.join(ROOT, "tests", "golden", "coeffs.json")))["poly1"]
+    cfg = oracle.make_config("poly1", co[:2], "opacity")
+    sc = oracle.activate(raw)
+    tx = (cam["width"] + 15) // 16
+    ty = (cam["height"] + 15) // 16
+    rng = np.random.default_rng(seed)
+    tiles = rng.choice(tx * ty, n_tiles, replace=False).tolist()
+    t0 = time.perf_counter()
+    s2d = oracle.project(sc, oc, cfg)
+    t1 = time.perf_counter()
+    oracle.render_tiled(sc, oc, cfg, tiles=tiles, s2d=s2d)
+    t2 = time.perf_counter()
+    frame = (t1 - t0) + (t2 - t1) * (tx * ty) / n_tiles
+    desc = (f"FP64 oracle, camera {seed % 16}: projection of all {sc['means'].shape[0]} splats + "
+            f"tile-binned render of {n_tiles} of {tx * ty} tiles, extrapolated to the frame")
+    return frame, t2 - t0, desc
+
+
+def run_reference(a, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2603_18707_b300 import synth
+    oracle.build()
+    raw = synth.scene_clusters(a.splats, 0, sh_degree=3)
+    cams = synth.orbit_cameras(a.cams, a.width, a.height)
+    for i in range(a.warmup):
+        oracle_sample(raw, cams[i % len(cams)], 8, seed=i)
+    frames = []
+    for i in range(a.steps):
+        f, _, desc = oracle_sample(raw, cams[i % len(cams)], 8, seed=i)
+        frames.append(f)
+    step_s = sum(frames) / len(frames) * a.cams  # one step = all cameras
+    fps = a.cams / step_s
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": step_s * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload(a),
+            "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                             "sample": desc.replace("camera 0", "camera k") +
+                             "; one step = one such sample per camera"},
+            "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(a, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2603_18707_b300 import api, render, synth
+    from paper_2603_18707_b300 import build as _build
+
+    torch.cuda.set_device(local)
+    _build.build()
+    raw = synth.scene_clusters(a.splats, 0, sh_degree=3)
+    cams = synth.orbit_cameras(a.cams, a.width, a.height)
+    sc = render.activate(raw)
+    P = a.splats
+    R = {"poly1": render.Rasterizer(cams, api.make_config("poly1", "opacity"), P),
+         "exp": render.Rasterizer(cams, api.make_config("exp", "opacity"), P)}
+    evals, psnr = {}, []
+    for k, r in R.items():
+        r.forward(sc, n_eval=True)  # sizes the overlap buffers, counts evaluations
+        evals[k] = int(r.n_eval.to(torch.int64).sum().item())
+    for ip, ie in zip(R["poly1"].images(), R["exp"].images()):
+        mse = torch.mean((ip - ie) ** 2).item()
+        psnr.append(-10 * math.log10(max(mse, 1e-30)))
+    overlaps = {k: R[k].n_records()[1] for k in R}
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        return e0.elapsed_time(e1) / steps
+
+    res, clocks, launches = {}, None, None
+    for k in ("poly1", "exp"):
+        r = R[k]
+        for _ in range(a.warmup):
+            r.run_async(sc)
+        if k == "poly1":
+            l0 = api.gs_launch_count()
+            with ClockSampler(local) as cs:
+                ms = timed(lambda: r.run_async(sc), a.steps)
+            clocks = cs.summary()
+            launches = api.gs_launch_count() - l0
+        else:
+            ms = timed(lambda: r.run_async(sc), a.steps)
+        res[k] = max_over_ranks(ms, world)
+
+    # per-stage device times (CUDA events between the entry points, same stream)
+    stages = {}
+    for k in ("poly1", "exp"):
+        r = R[k]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        acc = [0.0, 0.0, 0.0]
+        reps = max(5, a.steps // 4)
+        torch.cuda.synchronize()
+        for _ in range(reps):
+            ev[0].record(stream)
+            r.preprocess(sc)
+            ev[1].record(stream)
+            r.bin_sort()
+            ev[2].record(stream)
+            r.blend(n_eval=False)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            for i in range(3):
+                acc[i] += ev[i].elapsed_time(ev[i + 1])
+        stages[k] = {"preprocess_ms": acc[0] / reps, "bin_sort_ms": acc[1] / reps,
+                     "blend_ms": acc[2] / reps}
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not a.no_e2e:
+        host = {k: sc[k].cpu().pin_memory() for k in ("means", "scales", "quats", "opacities", "sh")}
+        dev = {k: torch.empty_like(sc[k]) for k in host}
+        dev["sh_degree"] = 3
+        out_host = torch.empty_like(R["poly1"].out, device="cpu").pin_memory()
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        d2h = out_host.numel() * out_host.element_size()
+        r = R["poly1"]
+
+        def e2e_step():
+            for k2, v in host.items():
+                dev[k2].copy_(v, non_blocking=True)
+            r.run_async(dev)
+            out_host.copy_(r.out, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        steps_e2e = max(3, a.steps // 4)
+        ms_e2e = max_over_ranks(timed(e2e_step, steps_e2e), world)
+        e2e = {"value": world * a.cams / (ms_e2e / 1e3), "unit": "frames/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
+
+    # roofline of the dominant kernel: the blend, bound by the FP32 pipes
+    st = stages["poly1"]
+    dom = max(st, key=st.get)
+    peak = SMS * FP32_LANES * 2 * 2032e6 / 1e12
+    blend_s = st["blend_ms"] / 1e3
+    achieved = evals["poly1"] * FLOP_PER_EVAL["poly1"] / blend_s / 1e12
+    roofline = {"bound": "alu", "kernel": "blend (render_kernel<POLY1>)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz (derived)",
+                "dominant_stage": dom}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        import oracle
+        oracle.build()
+        frame_s, sample_s, desc = oracle_sample(raw, cams[0], 64)
+        cpu = {"value": 1.0 / frame_s, "unit": "frames/s", "cores": os.cpu_count(),
+               "kind": "oracle", "sample": desc + f" ({sample_s:.1f} s of CPU time)"}
+
+    if rank != 0:
+        return
+    ms = res["poly1"]
+    fps = world * a.cams / (ms / 1e3)
+    line = {"metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload(a),
+            "gsplat_evals_per_s": world * evals["poly1"] / (ms / 1e3) / 1e9,
+            "exp": {"frames_per_s": world * a.cams / (res["exp"] / 1e3), "ms_per_step": res["exp"],
+                    "gsplat_evals_per_s": world * evals["exp"] / (res["exp"] / 1e3) / 1e9},
+            "speedup_poly1_vs_exp": res["exp"] / ms,
+            "psnr_poly1_vs_exp_db": {"mean": float(np.mean(psnr)), "min": float(np.min(psnr))},
+            "evals_per_step": evals, "overlaps_per_step": overlaps, "stages_ms": stages,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    world, rank, local = dist_setup(a)
+    if a.impl == "reference":
+        run_reference(a, world, rank)
+    else:
+        run_ours(a, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
