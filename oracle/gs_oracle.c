@@ -676,6 +676,8 @@ void orc_render_backward(int P, const double *means, const double *scales,
         for (int x = 0; x < W; ++x) {
             double px = x + 0.5, py = y + 0.5;
             const double *g = dL_dimg + 3 * ((long long)y * W + x);
+            /* a pixel with zero upstream gradient contributes nothing */
+            if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0) continue;
             double T = 1.0;
             int m = 0;
             for (int j = 0; j < n; ++j) {

@@ -1,0 +1,53 @@
+"""torch.autograd.Function over the C ABI: forward = gs_preprocess +
+gs_bin_sort + gs_render, backward = gs_render_backward.
+
+The library consumes activated values (scales, opacities, any-norm
+quaternions); `render` applies the 3DGS activations (exp of log-scales,
+sigmoid of opacity logits) in torch so that autograd chains through them.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import api
+from .render import Rasterizer
+
+
+class RenderFunction(torch.autograd.Function):
+    """Images of one Rasterizer's cameras, [sum H W, 3], differentiable in
+    means, scales, quats, opacities and SH. The rasterizer keeps the forward
+    state (records, sorted lists, final T, last contributor) that the backward
+    reads: run backward before the next forward on the same rasterizer."""
+
+    @staticmethod
+    def forward(ctx, means, scales, quats, opacities, sh, rasterizer: Rasterizer, sh_degree: int, bg):
+        sc = {"means": means.contiguous(), "scales": scales.contiguous(),
+              "quats": quats.contiguous(), "opacities": opacities.contiguous(),
+              "sh": sh.contiguous(), "sh_degree": int(sh_degree)}
+        out = rasterizer.forward(sc, bg, n_eval=False)
+        ctx.rasterizer = rasterizer
+        ctx.sh_degree = int(sh_degree)
+        ctx.bg = tuple(float(v) for v in bg)
+        ctx.save_for_backward(sc["means"], sc["scales"], sc["quats"], sc["opacities"], sc["sh"])
+        return out.clone()
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        means, scales, quats, opacities, sh = ctx.saved_tensors
+        R = ctx.rasterizer
+        g = {k: torch.zeros_like(v) for k, v in
+             (("means", means), ("scales", scales), ("quats", quats), ("opacities", opacities),
+              ("sh", sh))}
+        grad2d = torch.empty(api.gs_grad2d_bytes(R.ncam, R.P), dtype=torch.uint8,
+                             device=means.device)
+        api.gs_render_backward(R.cams, R.P, R.cfg, means, scales, quats, opacities, sh,
+                               ctx.sh_degree, R.splat2d, R.vals, R.ranges, ctx.bg, R.final_T,
+                               R.last, grad_out.contiguous(), grad2d, g["means"], g["scales"],
+                               g["quats"], g["opacities"], g["sh"])
+        return g["means"], g["scales"], g["quats"], g["opacities"], g["sh"], None, None, None
+
+
+def render(means, log_scales, quats, opacity_logits, sh, sh_degree, rasterizer, bg=(0.0, 0.0, 0.0)):
+    """Differentiable render from raw 3DGS parameters."""
+    return RenderFunction.apply(means, torch.exp(log_scales), quats, torch.sigmoid(opacity_logits),
+                                sh, rasterizer, sh_degree, bg)

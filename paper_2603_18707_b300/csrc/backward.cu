@@ -1,20 +1,490 @@
-// backward.cu — reverse pass (placeholder until the reverse kernels land).
+// backward.cu — reverse pass of the blend and of the projection (sm_103a).
+//
+// Stage 1, per tile (one CTA, one thread per pixel): walk the tile's list
+// backwards from the block's furthest last contributor. Each pixel starts
+// from its saved final transmittance and recovers T before every contributor
+// as T / (1 - alpha), recomputing alpha with exactly the forward arithmetic so
+// that every skip / clamp decision is the forward's. Per contributor:
+//   dL/dc = alpha T g,  dL/dalpha = sum_ch g (c T - S / (1 - alpha)),
+//   with S the colour behind it (later contributors plus T_final bg);
+//   alpha = o' k(Q) unclamped: dL/do' = k dL/dalpha, dL/dQ = o' k'(Q) dL/dalpha,
+//   k' = -k/2 (exp), c1 + 2 c2 Q + 3 c3 Q^2 (polynomials; the ReLU / cut are
+//   inactive wherever alpha >= eps), then dQ to the conic and the 2D mean.
+// The warp sums its lanes' contributions with shuffles and one lane adds them
+// to the record's 2D gradient with FP32 atomics.
+//
+// Stage 2, per splat (one thread, loop over cameras): the chain rule through
+// the projection written in preprocess.cu: colour clamp and SH (and the view
+// direction), o' = o rho with the AA factor (Sec. 3.4), conic = inverse of the
+// low-passed covariance, Sigma' = J W Sigma W^T J^T with the clamped
+// Jacobian, the pinhole mean, Sigma = R S S^T R^T, the quaternion
+// normalisation. Gradients are added to the caller's buffers.
 #include "gs_common.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kG2 = 12; // floats per record in the 2D gradient buffer
+// layout: dmean.x, dmean.y, dA, dB, dC, do', dr, dg, db, (unused x3)
+
+template <int KIND>
+__device__ __forceinline__ float kval(const CfgDev &cfg, float Q)
+{
+    if (KIND == GS_K_EXP) return __expf(-0.5f * Q);
+    if (KIND == GS_K_POLY1) return fmaf(cfg.c[1], Q, cfg.c[0]);
+    if (KIND == GS_K_POLY2) return Q < cfg.x0 ? fmaf(fmaf(cfg.c[2], Q, cfg.c[1]), Q, cfg.c[0]) : 0.f;
+    return fmaf(fmaf(fmaf(cfg.c[3], Q, cfg.c[2]), Q, cfg.c[1]), Q, cfg.c[0]);
+}
+
+template <int KIND>
+__device__ __forceinline__ float kderiv(const CfgDev &cfg, float Q, float k)
+{
+    if (KIND == GS_K_EXP) return -0.5f * k;
+    if (KIND == GS_K_POLY1) return cfg.c[1];
+    if (KIND == GS_K_POLY2) return fmaf(2.f * cfg.c[2], Q, cfg.c[1]);
+    return fmaf(fmaf(3.f * cfg.c[3], Q, 2.f * cfg.c[2]), Q, cfg.c[1]);
+}
+
+__device__ __forceinline__ float wsum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256)
+blend_backward_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
+                      const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
+                      const uint2 *__restrict__ ranges, uint32_t n_records, float bg0, float bg1,
+                      float bg2, const float *__restrict__ final_T, const uint32_t *__restrict__ last,
+                      const float *__restrict__ grad_out, float *__restrict__ grad2d)
+{
+    __shared__ float4 s_g[256];
+    __shared__ float4 s_q[256];
+    __shared__ float4 s_c[256];
+    __shared__ uint32_t s_id[256];
+    __shared__ uint32_t s_maxL;
+    const int gtile = blockIdx.x;
+    int c = 0;
+    while (c + 1 < cams.ncam && cams.cam[c + 1].tile_base <= gtile) ++c;
+    const CamDev &cm = cams.cam[c];
+    const int lt = gtile - cm.tile_base;
+    const int tx = lt % cm.tiles_x, ty = lt / cm.tiles_x;
+    const int px = tx * cfg.tile_w + (int)threadIdx.x % cfg.tile_w;
+    const int py = ty * cfg.tile_h + (int)threadIdx.x / cfg.tile_w;
+    const bool inside = px < cm.W && py < cm.H;
+    const float pxc = px + 0.5f, pyc = py + 0.5f;
+    const uint2 rg = ranges[gtile];
+    const int lane = threadIdx.x & 31;
+
+    float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    uint32_t L = 0;
+    if (inside) {
+        const int64_t pix = cm.pix_base + (int64_t)py * cm.W + px;
+        T = final_T[pix];
+        L = last[pix];
+        g0 = grad_out[3 * pix + 0];
+        g1 = grad_out[3 * pix + 1];
+        g2 = grad_out[3 * pix + 2];
+    }
+    float S0 = T * bg0, S1 = T * bg1, S2 = T * bg2;
+    if (threadIdx.x == 0) s_maxL = 0;
+    __syncthreads();
+    if (L) atomicMax(&s_maxL, L);
+    __syncthreads();
+    const int maxL = (int)s_maxL;
+    const int B = blockDim.x;
+    const float eps = cfg.eps, amax = cfg.alpha_max;
+    for (int end = maxL; end > 0; end -= B) {
+        const int start = max(0, end - B);
+        const int i = start + (int)threadIdx.x;
+        if (i < end) {
+            uint32_t v = vals[rg.x + i];
+            if (v >= n_records) v = 0;
+            s_id[threadIdx.x] = v;
+            s_g[threadIdx.x] = rec[3 * (size_t)v + 0];
+            s_q[threadIdx.x] = rec[3 * (size_t)v + 1];
+            s_c[threadIdx.x] = rec[3 * (size_t)v + 2];
+        }
+        __syncthreads();
+        for (int j = end - 1; j >= start; --j) {
+            const int jj = j - start;
+            const float4 g = s_g[jj];
+            const float4 q = s_q[jj];
+            const float dx = g.x - pxc, dy = g.y - pyc;
+            const float Q = fmaf(fmaf(q.x, dx, 2.f * q.y * dy), dx, q.z * dy * dy);
+            const float k = kval<KIND>(cfg, Q);
+            const float a0 = g.z * k;
+            const float a = fminf(amax, a0);
+            const bool contrib = (uint32_t)j < L && a >= eps;
+            float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (contrib) {
+                const float4 col = s_c[jj];
+                const float oma = 1.f - a;
+                T = T / oma;
+                const float w = a * T;
+                v[6] = w * g0;
+                v[7] = w * g1;
+                v[8] = w * g2;
+                const float ioma = 1.f / oma;
+                const float da = g0 * (col.x * T - S0 * ioma) + g1 * (col.y * T - S1 * ioma) +
+                                 g2 * (col.z * T - S2 * ioma);
+                S0 = fmaf(col.x, w, S0);
+                S1 = fmaf(col.y, w, S1);
+                S2 = fmaf(col.z, w, S2);
+                if (a0 <= amax) {
+                    v[5] = k * da;
+                    const float dQ = g.z * kderiv<KIND>(cfg, Q, k) * da;
+                    v[2] = dQ * dx * dx;
+                    v[3] = dQ * 2.f * dx * dy;
+                    v[4] = dQ * dy * dy;
+                    v[0] = dQ * 2.f * (q.x * dx + q.y * dy);
+                    v[1] = dQ * 2.f * (q.y * dx + q.z * dy);
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+#pragma unroll
+                for (int t = 0; t < 9; ++t) v[t] = wsum(v[t]);
+                if (lane == 0) {
+                    float *dst = grad2d + (size_t)s_id[jj] * kG2;
+#pragma unroll
+                    for (int t = 0; t < 9; ++t)
+                        if (v[t] != 0.f) atomicAdd(dst + t, v[t]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---- stage 2: per-splat chain rule ---------------------------------------
+
+constexpr float kY0 = 0.28209479177387814f;
+constexpr float kY1 = 0.48860251190291992f;
+constexpr float kY2a = 1.0925484305920792f;
+constexpr float kY2b = 0.31539156525252005f;
+constexpr float kY2c = 0.54627421529603959f;
+constexpr float kY3a = 0.59004358992664352f;
+constexpr float kY3b = 2.8906114426405538f;
+constexpr float kY3c = 0.45704579946446572f;
+constexpr float kY3d = 0.37317633259011546f;
+constexpr float kY3e = 1.4453057213202769f;
+
+// SH basis values Y[k] and their gradients with respect to the unit
+// direction, G[k][0..2] (3DGS order and signs).
+template <int D>
+__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float *Y, float (*G)[3])
+{
+    Y[0] = kY0;
+    G[0][0] = G[0][1] = G[0][2] = 0.f;
+    if (D >= 1) {
+        Y[1] = -kY1 * y; G[1][0] = 0.f; G[1][1] = -kY1; G[1][2] = 0.f;
+        Y[2] = kY1 * z;  G[2][0] = 0.f; G[2][1] = 0.f;  G[2][2] = kY1;
+        Y[3] = -kY1 * x; G[3][0] = -kY1; G[3][1] = 0.f; G[3][2] = 0.f;
+    }
+    if (D >= 2) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = kY2a * x * y;  G[4][0] = kY2a * y; G[4][1] = kY2a * x; G[4][2] = 0.f;
+        Y[5] = -kY2a * y * z; G[5][0] = 0.f; G[5][1] = -kY2a * z; G[5][2] = -kY2a * y;
+        Y[6] = kY2b * (2.f * zz - xx - yy);
+        G[6][0] = -2.f * kY2b * x; G[6][1] = -2.f * kY2b * y; G[6][2] = 4.f * kY2b * z;
+        Y[7] = -kY2a * x * z; G[7][0] = -kY2a * z; G[7][1] = 0.f; G[7][2] = -kY2a * x;
+        Y[8] = kY2c * (xx - yy); G[8][0] = 2.f * kY2c * x; G[8][1] = -2.f * kY2c * y; G[8][2] = 0.f;
+        if (D >= 3) {
+            Y[9] = -kY3a * y * (3.f * xx - yy);
+            G[9][0] = -kY3a * 6.f * x * y; G[9][1] = -kY3a * (3.f * xx - 3.f * yy); G[9][2] = 0.f;
+            Y[10] = kY3b * x * y * z;
+            G[10][0] = kY3b * y * z; G[10][1] = kY3b * x * z; G[10][2] = kY3b * x * y;
+            Y[11] = -kY3c * y * (4.f * zz - xx - yy);
+            G[11][0] = kY3c * 2.f * x * y; G[11][1] = -kY3c * (4.f * zz - xx - 3.f * yy);
+            G[11][2] = -kY3c * 8.f * y * z;
+            Y[12] = kY3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+            G[12][0] = -kY3d * 6.f * x * z; G[12][1] = -kY3d * 6.f * y * z;
+            G[12][2] = kY3d * (6.f * zz - 3.f * xx - 3.f * yy);
+            Y[13] = -kY3c * x * (4.f * zz - xx - yy);
+            G[13][0] = -kY3c * (4.f * zz - 3.f * xx - yy); G[13][1] = kY3c * 2.f * x * y;
+            G[13][2] = -kY3c * 8.f * x * z;
+            Y[14] = kY3e * z * (xx - yy);
+            G[14][0] = kY3e * 2.f * x * z; G[14][1] = -kY3e * 2.f * y * z; G[14][2] = kY3e * (xx - yy);
+            Y[15] = -kY3a * x * (xx - 3.f * yy);
+            G[15][0] = -kY3a * (3.f * xx - 3.f * yy); G[15][1] = kY3a * 6.f * x * y; G[15][2] = 0.f;
+        }
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(128)
+project_backward_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
+                        int P, const float *__restrict__ means, const float *__restrict__ scales,
+                        const float *__restrict__ quats, const float *__restrict__ opacities,
+                        const float *__restrict__ sh, const float *__restrict__ grad2d,
+                        float *__restrict__ g_means, float *__restrict__ g_scales,
+                        float *__restrict__ g_quats, float *__restrict__ g_opac,
+                        float *__restrict__ g_sh)
+{
+    constexpr int K = (D + 1) * (D + 1);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    const float mx = means[3 * i + 0], my = means[3 * i + 1], mz = means[3 * i + 2];
+    const float sx = scales[3 * i + 0], sy = scales[3 * i + 1], sz = scales[3 * i + 2];
+    const float4 q4 = reinterpret_cast<const float4 *>(quats)[i];
+    const float op = opacities[i];
+
+    const float qn = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
+    const float w = q4.x * qn, x = q4.y * qn, y = q4.z * qn, z = q4.w * qn;
+    float R[3][3] = {{1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y)},
+                     {2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x)},
+                     {2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)}};
+    const float s[3] = {sx, sy, sz};
+    float M[3][3], Sg[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) M[r][k] = R[r][k] * s[k];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Sg[r][k] = M[r][0] * M[k][0] + M[r][1] * M[k][1] + M[r][2] * M[k][2];
+
+    float dmean[3] = {0.f, 0.f, 0.f}, dSig[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float dop = 0.f;
+    float dsh[K * 3];
+#pragma unroll
+    for (int k = 0; k < K * 3; ++k) dsh[k] = 0.f;
+    bool any = false;
+
+    for (int c = 0; c < cams.ncam; ++c) {
+        const CamDev &cm = cams.cam[c];
+        const int64_t n = (int64_t)c * P + i;
+        const float4 ga = reinterpret_cast<const float4 *>(grad2d + n * kG2)[0];
+        const float4 gb = reinterpret_cast<const float4 *>(grad2d + n * kG2)[1];
+        const float4 gc = reinterpret_cast<const float4 *>(grad2d + n * kG2)[2];
+        const float dmx = ga.x, dmy = ga.y, dA = ga.z, dB = ga.w, dC = gb.x, do2 = gb.y;
+        const float dcol[3] = {gb.z, gb.w, gc.x};
+        if (dmx == 0.f && dmy == 0.f && dA == 0.f && dB == 0.f && dC == 0.f && do2 == 0.f &&
+            dcol[0] == 0.f && dcol[1] == 0.f && dcol[2] == 0.f)
+            continue;
+        any = true;
+        const float *W = cm.R;
+        const float tx = W[0] * mx + W[1] * my + W[2] * mz + cm.T[0];
+        const float ty = W[3] * mx + W[4] * my + W[5] * mz + cm.T[1];
+        const float tz = W[6] * mx + W[7] * my + W[8] * mz + cm.T[2];
+        const float iz = 1.f / tz;
+        const float rx = tx * iz, ry = ty * iz;
+        const int clx = rx < -cm.limx ? -1 : (rx > cm.limx ? 1 : 0);
+        const int cly = ry < -cm.limy ? -1 : (ry > cm.limy ? 1 : 0);
+        const float ux = fminf(fmaxf(rx, -cm.limx), cm.limx);
+        const float uy = fminf(fmaxf(ry, -cm.limy), cm.limy);
+        const float a0 = cm.fx * iz, b0 = cm.fy * iz;
+        float Tm[2][3] = {{a0 * (W[0] - ux * W[6]), a0 * (W[1] - ux * W[7]), a0 * (W[2] - ux * W[8])},
+                          {b0 * (W[3] - uy * W[6]), b0 * (W[4] - uy * W[7]), b0 * (W[5] - uy * W[8])}};
+        float TS[2][3];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                TS[r][k] = Tm[r][0] * Sg[0][k] + Tm[r][1] * Sg[1][k] + Tm[r][2] * Sg[2][k];
+        const float c00 = TS[0][0] * Tm[0][0] + TS[0][1] * Tm[0][1] + TS[0][2] * Tm[0][2];
+        const float c01 = TS[1][0] * Tm[0][0] + TS[1][1] * Tm[0][1] + TS[1][2] * Tm[0][2];
+        const float c11 = TS[1][0] * Tm[1][0] + TS[1][1] * Tm[1][1] + TS[1][2] * Tm[1][2];
+        const float a = c00 + cfg.dil, b = c01, cc = c11 + cfg.dil;
+        const float det0 = c00 * c11 - c01 * c01;
+        const float det1 = a * cc - b * b;
+        const float rho = cfg.aa ? sqrtf(fmaxf(det0, 0.f) / det1) : 1.f;
+
+        // colour: c = max(sum_k Y_k sh_k + 0.5, 0)
+        float dvx = mx - cm.campos[0], dvy = my - cm.campos[1], dvz = mz - cm.campos[2];
+        const float il = rsqrtf(dvx * dvx + dvy * dvy + dvz * dvz);
+        const float ex = dvx * il, ey = dvy * il, ez = dvz * il;
+        float Y[K], GY[K][3];
+        sh_basis_grad<D>(ex, ey, ez, Y, GY);
+        float draw[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc = fmaf(Y[k], sh[((size_t)i * K + k) * 3 + ch], acc);
+            draw[ch] = (acc + 0.5f > 0.f) ? dcol[ch] : 0.f;
+        }
+        float ddir[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            float t = 0.f;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                dsh[3 * k + ch] = fmaf(Y[k], draw[ch], dsh[3 * k + ch]);
+                t = fmaf(sh[((size_t)i * K + k) * 3 + ch], draw[ch], t);
+            }
+            ddir[0] = fmaf(GY[k][0], t, ddir[0]);
+            ddir[1] = fmaf(GY[k][1], t, ddir[1]);
+            ddir[2] = fmaf(GY[k][2], t, ddir[2]);
+        }
+        const float dd = ddir[0] * ex + ddir[1] * ey + ddir[2] * ez;
+        dmean[0] += (ddir[0] - ex * dd) * il;
+        dmean[1] += (ddir[1] - ey * dd) * il;
+        dmean[2] += (ddir[2] - ez * dd) * il;
+
+        // o' = o rho
+        dop += rho * do2;
+        const float drho = cfg.aa ? op * do2 : 0.f;
+        // conic = (Sigma' + vI)^-1
+        const float idet = 1.f / det1;
+        float ddet1 = -(dA * cc - dB * b + dC * a) * idet * idet;
+        float da = dC * idet, db = -dB * idet, dc = dA * idet;
+        float ddet0 = 0.f;
+        if (cfg.aa && det0 > 0.f) {
+            ddet0 = drho / (2.f * sqrtf(det0 * det1));
+            ddet1 += -drho * rho * 0.5f * idet;
+        }
+        da += ddet1 * cc;
+        dc += ddet1 * a;
+        db += -2.f * b * ddet1;
+        const float dS00 = da + ddet0 * c11, dS11 = dc + ddet0 * c00, dS01 = db - 2.f * c01 * ddet0;
+        const float G[2][2] = {{dS00, 0.5f * dS01}, {0.5f * dS01, dS11}};
+        // Sigma' = Tm Sigma Tm^T
+        float dTm[2][3];
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) dTm[r][k] = 2.f * (G[r][0] * TS[0][k] + G[r][1] * TS[1][k]);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                float acc = 0.f;
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+#pragma unroll
+                    for (int vv = 0; vv < 2; ++vv) acc += Tm[u][r] * G[u][vv] * Tm[vv][k];
+                dSig[r][k] += acc;
+            }
+        // Tm = J W with J = [[a0, 0, -a0 ux], [0, b0, -b0 uy]]
+        const float dJ00 = dTm[0][0] * W[0] + dTm[0][1] * W[1] + dTm[0][2] * W[2];
+        const float dJ02 = dTm[0][0] * W[6] + dTm[0][1] * W[7] + dTm[0][2] * W[8];
+        const float dJ11 = dTm[1][0] * W[3] + dTm[1][1] * W[4] + dTm[1][2] * W[5];
+        const float dJ12 = dTm[1][0] * W[6] + dTm[1][1] * W[7] + dTm[1][2] * W[8];
+        const float txc = ux * tz, tyc = uy * tz;
+        const float iz2 = iz * iz, iz3 = iz2 * iz;
+        float dtx = 0.f, dty = 0.f;
+        float dtz = -cm.fx * iz2 * dJ00 + 2.f * cm.fx * txc * iz3 * dJ02 - cm.fy * iz2 * dJ11 +
+                    2.f * cm.fy * tyc * iz3 * dJ12;
+        const float dtxc = -cm.fx * iz2 * dJ02, dtyc = -cm.fy * iz2 * dJ12;
+        if (clx == 0) dtx += dtxc; else dtz += clx * cm.limx * dtxc;
+        if (cly == 0) dty += dtyc; else dtz += cly * cm.limy * dtyc;
+        // mean2d = (fx tx / tz + cx, fy ty / tz + cy)
+        dtx += cm.fx * iz * dmx;
+        dty += cm.fy * iz * dmy;
+        dtz += -cm.fx * tx * iz2 * dmx - cm.fy * ty * iz2 * dmy;
+        // t = W mu + T
+        dmean[0] += W[0] * dtx + W[3] * dty + W[6] * dtz;
+        dmean[1] += W[1] * dtx + W[4] * dty + W[7] * dtz;
+        dmean[2] += W[2] * dtx + W[5] * dty + W[8] * dtz;
+    }
+    if (!any) return;
+
+    // Sigma = M M^T, M = R diag(s): dM = (dSig + dSig^T) M
+    float ds[3] = {0.f, 0.f, 0.f}, dR[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float dM = (dSig[r][0] + dSig[0][r]) * M[0][k] + (dSig[r][1] + dSig[1][r]) * M[1][k] +
+                             (dSig[r][2] + dSig[2][r]) * M[2][k];
+            ds[k] += dM * R[r][k];
+            dR[r][k] = dM * s[k];
+        }
+    float dqn[4];
+    dqn[0] = 2.f * (-z * dR[0][1] + y * dR[0][2] + z * dR[1][0] - x * dR[1][2] - y * dR[2][0] + x * dR[2][1]);
+    dqn[1] = 2.f * (y * dR[0][1] + z * dR[0][2] + y * dR[1][0] - 2.f * x * dR[1][1] - w * dR[1][2] +
+                    z * dR[2][0] + w * dR[2][1] - 2.f * x * dR[2][2]);
+    dqn[2] = 2.f * (-2.f * y * dR[0][0] + x * dR[0][1] + w * dR[0][2] + x * dR[1][0] + z * dR[1][2] -
+                    w * dR[2][0] + z * dR[2][1] - 2.f * y * dR[2][2]);
+    dqn[3] = 2.f * (-2.f * z * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] - 2.f * z * dR[1][1] +
+                    y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
+    const float dot = dqn[0] * w + dqn[1] * x + dqn[2] * y + dqn[3] * z;
+    const float qv[4] = {w, x, y, z};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) g_quats[4 * i + k] += (dqn[k] - qv[k] * dot) * qn;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        g_means[3 * i + k] += dmean[k];
+        g_scales[3 * i + k] += ds[k];
+    }
+    g_opac[i] += dop;
+#pragma unroll
+    for (int k = 0; k < K * 3; ++k) g_sh[(size_t)i * K * 3 + k] += dsh[k];
+}
+
+} // namespace
+} // namespace gs
 
 using namespace gs;
 
 extern "C" size_t gs_grad2d_bytes(int32_t ncam, int32_t P)
 {
     if (ncam <= 0 || P < 0) return 0;
-    return align256(sizeof(float) * 12 * (size_t)ncam * P);
+    return align256(sizeof(float) * kG2 * (size_t)ncam * P);
 }
 
-extern "C" gs_status gs_render_backward(void *, const gs_camera *, int32_t, int32_t, const gs_config *,
-                                        const float *, const float *, const float *, const float *,
-                                        const float *, int32_t, const void *, const uint32_t *,
-                                        const uint32_t *, const float *, const float *,
-                                        const uint32_t *, const float *, void *, float *, float *,
-                                        float *, float *, float *)
+extern "C" gs_status gs_render_backward(void *stream, const gs_camera *cams, int32_t ncam, int32_t P,
+                                        const gs_config *cfg, const float *d_means,
+                                        const float *d_scales, const float *d_quats,
+                                        const float *d_opacities, const float *d_sh,
+                                        int32_t sh_degree, const void *d_splat2d,
+                                        const uint32_t *d_vals, const uint32_t *d_ranges,
+                                        const float *bg, const float *d_final_T,
+                                        const uint32_t *d_last, const float *d_grad_out,
+                                        void *d_grad2d, float *d_grad_means, float *d_grad_scales,
+                                        float *d_grad_quats, float *d_grad_opacities,
+                                        float *d_grad_sh)
 {
-    return GS_ERR_UNSUPPORTED;
+    if (!cams || !cfg || !bg || ncam <= 0 || ncam > kMaxCams || P < 0 || sh_degree < 0 || sh_degree > 3)
+        return GS_ERR_ARG;
+    if (P == 0) return GS_OK;
+    if (!d_means || !d_scales || !d_quats || !d_opacities || !d_sh || !d_splat2d || !d_vals ||
+        !d_ranges || !d_final_T || !d_last || !d_grad_out || !d_grad2d || !d_grad_means ||
+        !d_grad_scales || !d_grad_quats || !d_grad_opacities || !d_grad_sh)
+        return GS_ERR_ARG;
+    if (((uintptr_t)d_quats & 15) || ((uintptr_t)d_splat2d & 255) || ((uintptr_t)d_grad2d & 15))
+        return GS_ERR_ARG;
+    CamTable t;
+    CfgDev c;
+    if (!build_cam_table(cams, ncam, cfg, &t) || !build_cfg(cfg, &c)) return GS_ERR_ARG;
+    if (cfg->tile_w * cfg->tile_h > 256) return GS_ERR_UNSUPPORTED;
+    const int64_t N = (int64_t)ncam * P;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_grad2d, 0, gs_grad2d_bytes(ncam, P), s) != cudaSuccess) return GS_ERR_CUDA;
+    const float4 *rec = splat2d_const(d_splat2d, N).rec;
+    const uint2 *rg = reinterpret_cast<const uint2 *>(d_ranges);
+    float *g2 = static_cast<float *>(d_grad2d);
+    const int threads = cfg->tile_w * cfg->tile_h;
+#define GS_BWD_LAUNCH(K)                                                                             \
+    blend_backward_kernel<K><<<t.total_tiles, threads, 0, s>>>(t, c, rec, d_vals, rg, (uint32_t)N,   \
+                                                               bg[0], bg[1], bg[2], d_final_T,       \
+                                                               d_last, d_grad_out, g2)
+    switch (cfg->kind) {
+    case GS_K_EXP: GS_BWD_LAUNCH(GS_K_EXP); break;
+    case GS_K_POLY1: GS_BWD_LAUNCH(GS_K_POLY1); break;
+    case GS_K_POLY2: GS_BWD_LAUNCH(GS_K_POLY2); break;
+    default: GS_BWD_LAUNCH(GS_K_POLY3); break;
+    }
+#undef GS_BWD_LAUNCH
+    count_launch();
+    GS_LAUNCH_CHECK();
+    const int pt = 128, pb = (P + pt - 1) / pt;
+#define GS_PBWD_LAUNCH(D)                                                                          \
+    project_backward_kernel<D><<<pb, pt, 0, s>>>(t, c, P, d_means, d_scales, d_quats, d_opacities, \
+                                                 d_sh, g2, d_grad_means, d_grad_scales,            \
+                                                 d_grad_quats, d_grad_opacities, d_grad_sh)
+    switch (sh_degree) {
+    case 0: GS_PBWD_LAUNCH(0); break;
+    case 1: GS_PBWD_LAUNCH(1); break;
+    case 2: GS_PBWD_LAUNCH(2); break;
+    default: GS_PBWD_LAUNCH(3); break;
+    }
+#undef GS_PBWD_LAUNCH
+    count_launch();
+    GS_LAUNCH_CHECK();
+    return GS_OK;
 }
