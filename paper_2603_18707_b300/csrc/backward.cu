@@ -93,7 +93,7 @@ blend_backward_kernel(const __grid_constant__ CamTable cams, const __grid_consta
     __syncthreads();
     if (L) atomicMax(&s_maxL, L);
     __syncthreads();
-    const int maxL = (int)s_maxL;
+    const int maxL = (int)min(s_maxL, rg.y - rg.x); // a pixel's last lies within its tile list
     const int B = blockDim.x;
     const float eps = cfg.eps, amax = cfg.alpha_max;
     for (int end = maxL; end > 0; end -= B) {
