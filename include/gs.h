@@ -200,6 +200,32 @@ gs_status gs_render_backward(void *stream, const gs_camera *cams, int32_t ncam, 
                              float *d_grad_means, float *d_grad_scales, float *d_grad_quats,
                              float *d_grad_opacities, float *d_grad_sh);
 
+/* gs_bin_sort for callers that cannot allocate device memory — a plugin
+ * whose host application owns all device allocations through its own pool,
+ * or a real-time frame loop that may not allocate once it is running. The
+ * paper has no counterpart; this is a deployment convenience of this library.
+ *
+ * Same arguments, results and errors as gs_bin_sort, minus the workspace: the
+ * scratch is one fixed array of GS_NOALLOC_WORKSPACE_BYTES in static device
+ * memory, reserved on every GPU that loads the library and held until the
+ * process exits. The call itself allocates nothing. Sizes whose workspace
+ * (gs_bin_sort_workspace_bytes(ncam * P, capacity, tiles): about 17 bytes
+ * per record plus 13 bytes per overlap of capacity) would not fit are
+ * rejected with GS_ERR_ARG before anything is launched.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current) and caches it: make that first call before any
+ *    stream capture.
+ *  - All calls on a device share the one array; each call clears the parts
+ *    that must start at zero. Calls that overlap on the GPU (other streams,
+ *    or host threads without ordering between them) race: serialise them.
+ *  - The device error word lives inside the static array; detect an
+ *    overflowing capacity from d_count (overlaps counted > capacity). */
+#define GS_NOALLOC_WORKSPACE_BYTES ((size_t)32 << 20)
+gs_status gs_bin_sort_noalloc(void *stream, const gs_camera *cams, int32_t ncam, int32_t P,
+                              const gs_config *cfg, const void *d_splat2d, int64_t capacity,
+                              uint32_t *d_vals, uint32_t *d_ranges, uint64_t *d_keys64,
+                              uint32_t *d_count);
+
 /* Reads (synchronously, on `stream`) the device error word of a bin/sort
  * workspace into *code (OR of GS_ERR_CAPACITY / GS_ERR_TIMEOUT) and clears
  * it. Returns GS_ERR_CUDA if the copy fails. */

@@ -54,6 +54,8 @@ _SIGS = {
     "gs_bin_sort_workspace_bytes": (_sz, [_i64, _i64, _i64]),
     "gs_bin_sort": (_i32, [_vp, C.POINTER(GsCamera), _i32, _i32, C.POINTER(GsConfig), _vp, _i64,
                            _vp, _sz, _vp, _vp, _vp, _vp]),
+    "gs_bin_sort_noalloc": (_i32, [_vp, C.POINTER(GsCamera), _i32, _i32, C.POINTER(GsConfig), _vp,
+                                   _i64, _vp, _vp, _vp, _vp]),
     "gs_render": (_i32, [_vp, C.POINTER(GsCamera), _i32, _i32, C.POINTER(GsConfig), _vp, _vp, _vp,
                          C.POINTER(C.c_float), _vp, _vp, _vp, _vp]),
     "gs_grad2d_bytes": (_sz, [_i32, _i32]),

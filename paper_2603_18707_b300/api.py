@@ -116,6 +116,17 @@ def gs_bin_sort(cams, P, cfg, splat2d, capacity, workspace, vals, ranges, keys64
         _p(keys64), _p(count)))
 
 
+def gs_bin_sort_noalloc(cams, P, cfg, splat2d, capacity, vals, ranges, keys64=None, count=None,
+                        stream=None):
+    """gs_bin_sort for callers that cannot allocate device memory: the
+    scratch is the library's static device array (GS_NOALLOC_WORKSPACE_BYTES),
+    shared by every call on a device."""
+    arr = camera_array(cams)
+    check("gs_bin_sort_noalloc", lib().gs_bin_sort_noalloc(
+        _stream(stream), arr, len(arr), int(P), C.byref(cfg), _p(splat2d), int(capacity),
+        _p(vals), _p(ranges), _p(keys64), _p(count)))
+
+
 def gs_render(cams, P, cfg, splat2d, vals, ranges, bg, out_rgb, final_T=None, last=None,
               n_eval=None, stream=None):
     arr = camera_array(cams)
