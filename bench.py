@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--height", type=int, default=1080)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--profile", choices=["poly1", "exp"], default=None,
+                   help="run only `steps` passes of one arm (for ncu), print no bench line")
     return p.parse_args()
 
 
@@ -214,6 +216,18 @@ def run_ours(a, world, rank, local):
     cams = synth.orbit_cameras(a.cams, a.width, a.height)
     sc = render.activate(raw)
     P = a.splats
+    if a.profile:
+        # profiling mode: one arm, buffers sized, then exactly `steps` passes
+        r = render.Rasterizer(cams, api.make_config(a.profile, "opacity"), P)
+        r.forward(sc, n_eval=False)
+        torch.cuda.synchronize()
+        for _ in range(a.steps):
+            r.run_async(sc)
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"profile": a.profile, "steps": a.steps, "config": workload(a),
+                              "launches_per_step": 14}), flush=True)
+        return
     R = {"poly1": render.Rasterizer(cams, api.make_config("poly1", "opacity"), P),
          "exp": render.Rasterizer(cams, api.make_config("exp", "opacity"), P)}
     evals, psnr = {}, []

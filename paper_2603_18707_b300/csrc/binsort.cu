@@ -42,7 +42,8 @@ constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems; // keys per partition
 constexpr int kCompactItems = 8;
 constexpr int kCompactTile = 256 * kCompactItems;
-constexpr int kEmitTile = 256;
+constexpr int kEmitItems = 8;
+constexpr int kEmitTile = 256 * kEmitItems;
 
 enum Counter {
     CTR_COMPACT = 0,
@@ -352,53 +353,79 @@ emit_kernel(const __grid_constant__ CamTable cams, int P, uint32_t n_records,
     const uint32_t part = s_part;
     const uint32_t nparts = (nv + kEmitTile - 1) / kEmitTile;
     if (part >= nparts) return;
-    const int lane = threadIdx.x & 31;
-    const uint32_t j = part * kEmitTile + threadIdx.x;
-    uint32_t v = j < nv ? sorted_vals[j] : 0u;
-    const bool valid = j < nv && v < n_records; // ids are always < n_records unless a wait timed out
-    if (!valid) v = 0u;
-    const uint32_t cnt = valid ? tiles[v] : 0u;
-    const ushort4 rc = valid ? rects[v] : make_ushort4(0, 0, 0, 0);
-    uint32_t total;
-    const uint32_t excl_t = block_excl_scan(cnt, s_warp, total);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // warp-striped: item j of lane l is record wbase + 32 j + l (depth order)
+    const uint32_t wbase = part * kEmitTile + warp * (32 * kEmitItems);
+    uint32_t v[kEmitItems], cnt[kEmitItems], incl[kEmitItems], off[kEmitItems];
+    ushort4 rc[kEmitItems];
+    uint32_t running = 0;
+#pragma unroll
+    for (int j = 0; j < kEmitItems; ++j) {
+        const uint32_t idx = wbase + 32 * j + lane;
+        uint32_t vv = idx < nv ? sorted_vals[idx] : 0u;
+        const bool valid = idx < nv && vv < n_records; // ids are < n_records unless a wait timed out
+        if (!valid) vv = 0u;
+        v[j] = vv;
+        cnt[j] = valid ? tiles[vv] : 0u;
+        rc[j] = valid ? rects[vv] : make_ushort4(0, 0, 0, 0);
+        uint32_t x = cnt[j];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        incl[j] = x;
+        off[j] = running;
+        running += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) s_warp[warp] = running;
+    __syncthreads();
+    uint32_t warp_excl = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const uint32_t t = s_warp[w];
+        warp_excl += (w < warp) ? t : 0u;
+        total += t;
+    }
     if (threadIdx.x < 32) {
         const uint32_t e = lookback_scalar(state, part, total, &hdr->err);
         if (threadIdx.x == 0) s_excl = e;
     }
     __syncthreads();
     const uint32_t part_excl = s_excl;
-    // warp-local inclusive prefix of the counts
-    const uint32_t warp_first = __shfl_sync(0xffffffffu, excl_t, 0);
-    const uint32_t w_incl = excl_t - warp_first + cnt;
-    const uint32_t w_total = __shfl_sync(0xffffffffu, w_incl, 31);
-    const uint32_t out_base = part_excl + warp_first;
-    int cam = 0;
-    if (valid) cam = (int)(v / (uint32_t)P);
-    const int tiles_x = cams.cam[cam].tiles_x;
-    const uint32_t tbase = (uint32_t)cams.cam[cam].tile_base + (uint32_t)rc.y * tiles_x + rc.x;
-    const uint32_t rw = (uint32_t)rc.z - rc.x + 1u;
-    // the warp walks its overlaps 32 at a time; every lane takes part in
-    // every shuffle, lanes past the end only skip the store
-    for (uint32_t b = 0; b < w_total; b += 32) {
-        const uint32_t p = b + lane;
-        const uint32_t pq = min(p, w_total - 1u);
-        int e = 0; // owner lane: number of lanes whose inclusive prefix is <= pq
 #pragma unroll
-        for (int s = 16; s > 0; s >>= 1) {
-            const uint32_t c = __shfl_sync(0xffffffffu, w_incl, e + s - 1);
-            if (c <= pq) e += s;
-        }
-        const uint32_t ev = __shfl_sync(0xffffffffu, v, e);
-        const uint32_t ebeg = __shfl_sync(0xffffffffu, w_incl - cnt, e);
-        const uint32_t erw = __shfl_sync(0xffffffffu, rw, e);
-        const uint32_t etb = __shfl_sync(0xffffffffu, tbase, e);
-        const uint32_t etx = __shfl_sync(0xffffffffu, (uint32_t)tiles_x, e);
-        const uint32_t l = pq - ebeg;
-        const uint32_t row = l / erw, col = l - row * erw;
-        const uint32_t o = out_base + p;
-        if (p < w_total && o < capacity) {
-            keys_out[o] = etb + row * etx + col;
-            vals_out[o] = ev;
+    for (int j = 0; j < kEmitItems; ++j) {
+        const uint32_t w_incl = incl[j];
+        const uint32_t w_total = __shfl_sync(0xffffffffu, w_incl, 31);
+        const uint32_t out_base = part_excl + warp_excl + off[j];
+        const int cam = (int)(v[j] / (uint32_t)P);
+        const int tiles_x = cams.cam[cam].tiles_x;
+        const uint32_t tbase = (uint32_t)cams.cam[cam].tile_base + (uint32_t)rc[j].y * tiles_x + rc[j].x;
+        const uint32_t rw = (uint32_t)rc[j].z - rc[j].x + 1u;
+        const uint32_t beg = w_incl - cnt[j];
+        // the warp walks these overlaps 32 at a time; every lane takes part
+        // in every shuffle, lanes past the end only skip the store
+        for (uint32_t b = 0; b < w_total; b += 32) {
+            const uint32_t p = b + lane;
+            const uint32_t pq = min(p, w_total - 1u);
+            int e = 0; // owner lane: number of lanes whose inclusive prefix is <= pq
+#pragma unroll
+            for (int sft = 16; sft > 0; sft >>= 1) {
+                const uint32_t c = __shfl_sync(0xffffffffu, w_incl, e + sft - 1);
+                if (c <= pq) e += sft;
+            }
+            const uint32_t ev = __shfl_sync(0xffffffffu, v[j], e);
+            const uint32_t ebeg = __shfl_sync(0xffffffffu, beg, e);
+            const uint32_t erw = __shfl_sync(0xffffffffu, rw, e);
+            const uint32_t etb = __shfl_sync(0xffffffffu, tbase, e);
+            const uint32_t etx = __shfl_sync(0xffffffffu, (uint32_t)tiles_x, e);
+            const uint32_t l = pq - ebeg;
+            const uint32_t row = l / erw, col = l - row * erw;
+            const uint32_t o = out_base + p;
+            if (p < w_total && o < capacity) {
+                keys_out[o] = etb + row * etx + col;
+                vals_out[o] = ev;
+            }
         }
     }
     if (part == nparts - 1 && threadIdx.x == 0) {

@@ -47,6 +47,7 @@ class Rasterizer:
         self.last = torch.empty(self.npix, **i32)
         self.n_eval = torch.empty(self.npix, **i32)
         self.keep_keys = keep_keys
+        self.shrink = capacity is None  # an explicit capacity is kept as given
         self.capacity = 0
         self._alloc(capacity if capacity else max(1 << 20, 8 * self.ncam * self.P))
 
@@ -72,17 +73,22 @@ class Rasterizer:
                       self.out, self.final_T, self.last, self.n_eval if n_eval else None)
 
     def forward(self, sc: dict, bg=(0.0, 0.0, 0.0), n_eval: bool = True):
-        """One pass of the whole path; grows the overlap buffer if needed."""
-        for _ in range(3):
+        """One pass of the whole path; grows the overlap buffer when it was
+        too small and shrinks it when it is far too large (the sort's grids
+        and look-back state scale with the capacity), then reruns."""
+        for _ in range(4):
             self.preprocess(sc)
             self.bin_sort()
             self.blend(bg, n_eval)
             err = api.gs_workspace_status(self.workspace)
+            need = int(self.count[2].item() & 0xFFFFFFFF)
             if not err & GS_ERR_CAPACITY:
                 if err:
                     raise RuntimeError(f"device error word {err}")
+                if self.shrink and self.capacity > 2 * need + (1 << 16):
+                    self._alloc(int(need * 1.15) + 4096)
+                    continue
                 return self.out
-            need = int(self.count[2].item() & 0xFFFFFFFF)
             self._alloc(int(max(need, self.capacity) * 1.25) + 1024)
         raise RuntimeError("overlap capacity could not be sized")
 
