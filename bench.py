@@ -49,7 +49,9 @@ def parse():
     p.add_argument("--height", type=int, default=1080)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--profile", choices=["poly1", "exp"], default=None,
+    p.add_argument("--ppt", type=int, default=None, help="pixels per blend thread (1, 2, 4)")
+    p.add_argument("--tile", type=str, default=None, help="tile shape WxH, e.g. 16x16")
+    p.add_argument("--profile", choices=["poly1", "exp", "poly2", "poly3"], default=None,
                    help="run only `steps` passes of one arm (for ncu), print no bench line")
     return p.parse_args()
 
@@ -216,20 +218,29 @@ def run_ours(a, world, rank, local):
     cams = synth.orbit_cameras(a.cams, a.width, a.height)
     sc = render.activate(raw)
     P = a.splats
+    over = {}
+    if a.ppt:
+        over["px_per_thread"] = a.ppt
+    if a.tile:
+        over["tile"] = tuple(int(v) for v in a.tile.split("x"))
     if a.profile:
         # profiling mode: one arm, buffers sized, then exactly `steps` passes
-        r = render.Rasterizer(cams, api.make_config(a.profile, "opacity"), P)
+        r = render.Rasterizer(cams, api.make_config(a.profile, "opacity", **over), P)
         r.forward(sc, n_eval=False)
         torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record()
         for _ in range(a.steps):
             r.run_async(sc)
+        e[1].record()
         torch.cuda.synchronize()
         if rank == 0:
             print(json.dumps({"profile": a.profile, "steps": a.steps, "config": workload(a),
+                              "overrides": over, "ms_per_step": e[0].elapsed_time(e[1]) / max(a.steps, 1),
                               "launches_per_step": 14}), flush=True)
         return
-    R = {"poly1": render.Rasterizer(cams, api.make_config("poly1", "opacity"), P),
-         "exp": render.Rasterizer(cams, api.make_config("exp", "opacity"), P)}
+    R = {"poly1": render.Rasterizer(cams, api.make_config("poly1", "opacity", **over), P),
+         "exp": render.Rasterizer(cams, api.make_config("exp", "opacity", **over), P)}
     evals, psnr = {}, []
     for k, r in R.items():
         r.forward(sc, n_eval=True)  # sizes the overlap buffers, counts evaluations

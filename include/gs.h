@@ -122,7 +122,8 @@ gs_status gs_config_default(int32_t kind, int32_t cull, gs_config *cfg);
  *                      and rho the AA factor
  *   uint16 rect[N][4]  tile x0, y0, x1, y1 (inclusive) of the support rectangle
  *   uint32 tiles[N]    number of tiles in rect; 0 = splat not drawn
- *   uint32 dkey[N]     float bits of depth (drawn splats only)
+ *   uint32 dkey[N]     float bits of depth
+ *   rec, rect and dkey are written only for records with tiles > 0.
  * each array 256-byte aligned. */
 size_t gs_splat2d_bytes(int32_t ncam, int32_t P);
 

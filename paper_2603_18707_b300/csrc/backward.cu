@@ -19,31 +19,13 @@
 // low-passed covariance, Sigma' = J W Sigma W^T J^T with the clamped
 // Jacobian, the pinhole mean, Sigma = R S S^T R^T, the quaternion
 // normalisation. Gradients are added to the caller's buffers.
-#include "gs_common.cuh"
+#include "blend_math.cuh"
 
 namespace gs {
 namespace {
 
 constexpr int kG2 = 12; // floats per record in the 2D gradient buffer
 // layout: dmean.x, dmean.y, dA, dB, dC, do', dr, dg, db, (unused x3)
-
-template <int KIND>
-__device__ __forceinline__ float kval(const CfgDev &cfg, float Q)
-{
-    if (KIND == GS_K_EXP) return __expf(-0.5f * Q);
-    if (KIND == GS_K_POLY1) return fmaf(cfg.c[1], Q, cfg.c[0]);
-    if (KIND == GS_K_POLY2) return Q < cfg.x0 ? fmaf(fmaf(cfg.c[2], Q, cfg.c[1]), Q, cfg.c[0]) : 0.f;
-    return fmaf(fmaf(fmaf(cfg.c[3], Q, cfg.c[2]), Q, cfg.c[1]), Q, cfg.c[0]);
-}
-
-template <int KIND>
-__device__ __forceinline__ float kderiv(const CfgDev &cfg, float Q, float k)
-{
-    if (KIND == GS_K_EXP) return -0.5f * k;
-    if (KIND == GS_K_POLY1) return cfg.c[1];
-    if (KIND == GS_K_POLY2) return fmaf(2.f * cfg.c[2], Q, cfg.c[1]);
-    return fmaf(fmaf(3.f * cfg.c[3], Q, 2.f * cfg.c[2]), Q, cfg.c[1]);
-}
 
 __device__ __forceinline__ float wsum(float v)
 {
@@ -62,7 +44,9 @@ blend_backward_kernel(const __grid_constant__ CamTable cams, const __grid_consta
 {
     __shared__ float4 s_g[256];
     __shared__ float4 s_q[256];
-    __shared__ float4 s_c[256];
+    __shared__ float4 s_ka[256];
+    __shared__ float4 s_kb[256];
+    __shared__ float4 s_kc[256];
     __shared__ uint32_t s_id[256];
     __shared__ uint32_t s_maxL;
     const int gtile = blockIdx.x;
@@ -75,6 +59,9 @@ blend_backward_kernel(const __grid_constant__ CamTable cams, const __grid_consta
     const int py = ty * cfg.tile_h + (int)threadIdx.x / cfg.tile_w;
     const bool inside = px < cm.W && py < cm.H;
     const float pxc = px + 0.5f, pyc = py + 0.5f;
+    const float ox = (float)(tx * cfg.tile_w), oy = (float)(ty * cfg.tile_h);
+    const float xl = (float)((int)threadIdx.x % cfg.tile_w) + 0.5f;
+    const float yl = (float)((int)threadIdx.x / cfg.tile_w) + 0.5f;
     const uint2 rg = ranges[gtile];
     const int lane = threadIdx.x & 31;
 
@@ -103,24 +90,31 @@ blend_backward_kernel(const __grid_constant__ CamTable cams, const __grid_consta
             uint32_t v = vals[rg.x + i];
             if (v >= n_records) v = 0;
             s_id[threadIdx.x] = v;
-            s_g[threadIdx.x] = rec[3 * (size_t)v + 0];
-            s_q[threadIdx.x] = rec[3 * (size_t)v + 1];
-            s_c[threadIdx.x] = rec[3 * (size_t)v + 2];
+            const float4 r0 = rec[3 * (size_t)v + 0], r1 = rec[3 * (size_t)v + 1];
+            const BlendCoef kc = make_coef<KIND>(cfg, r0, r1, rec[3 * (size_t)v + 2], ox, oy);
+            s_g[threadIdx.x] = r0;
+            s_q[threadIdx.x] = r1;
+            s_ka[threadIdx.x] = kc.a;
+            s_kb[threadIdx.x] = kc.b;
+            s_kc[threadIdx.x] = kc.c;
         }
         __syncthreads();
         for (int j = end - 1; j >= start; --j) {
             const int jj = j - start;
-            const float4 g = s_g[jj];
-            const float4 q = s_q[jj];
-            const float dx = g.x - pxc, dy = g.y - pyc;
-            const float Q = fmaf(fmaf(q.x, dx, 2.f * q.y * dy), dx, q.z * dy * dy);
-            const float k = kval<KIND>(cfg, Q);
-            const float a0 = g.z * k;
+            // alpha exactly as the forward computed it
+            const float4 ka = s_ka[jj], kb = s_kb[jj];
+            const float u = fmaf(ka.x, xl, fmaf(ka.y, yl, ka.z));
+            const float vv = fmaf(ka.w, yl, kb.x);
+            const float Q = fmaf(u, u, vv * vv);
+            const float a0 = alpha_of_q<KIND>(cfg, kb, s_kc[jj].w, Q);
             const float a = fminf(amax, a0);
             const bool contrib = (uint32_t)j < L && a >= eps;
             float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (contrib) {
-                const float4 col = s_c[jj];
+                const float4 g = s_g[jj];
+                const float4 q = s_q[jj];
+                const float dx = g.x - pxc, dy = g.y - pyc;
+                const float4 col = s_kc[jj];
                 const float oma = 1.f - a;
                 T = T / oma;
                 const float w = a * T;
@@ -134,8 +128,8 @@ blend_backward_kernel(const __grid_constant__ CamTable cams, const __grid_consta
                 S1 = fmaf(col.y, w, S1);
                 S2 = fmaf(col.z, w, S2);
                 if (a0 <= amax) {
-                    v[5] = k * da;
-                    const float dQ = g.z * kderiv<KIND>(cfg, Q, k) * da;
+                    v[5] = a0 / g.z * da; // k(Q) = o' k(Q) / o'
+                    const float dQ = g.z * kernel_slope<KIND>(cfg, Q, a0, g.z) * da;
                     v[2] = dQ * dx * dx;
                     v[3] = dQ * 2.f * dx * dy;
                     v[4] = dQ * dy * dy;

@@ -6,24 +6,27 @@
 // index order gives. It is produced here without ever materialising 64-bit
 // keys:
 //   1. compact   drawn records (tiles > 0) -> (depth bits, record index),
-//                in index order (single-pass scan with decoupled look-back)
+//                in index order (single-pass scan with decoupled look-back);
+//                also histograms the four depth digits
 //   2. sort      stable LSD radix sort of those by depth: 4 Onesweep passes
 //   3. emit      walk the depth-sorted records, scan their tile counts and
 //                write one (tile id, record index) pair per covered tile;
-//                warp-cooperative so that every store is coalesced
-//   4. sort      stable LSD radix sort of the pairs by tile id:
-//                ceil(bits(total tiles) / 8) Onesweep passes
+//                warp-cooperative so that every store is coalesced; also
+//                histograms the tile-id digits
+//   4. sort      stable LSD radix sort of the pairs by tile id: 1 pass of 8
+//                bits, 2 of 8, 2 of 9 or 3 of 8-9 bits, whatever covers the
+//                tile ids
 //   5. ranges    first / one-past-last position of every tile id
 // The depth digits are sorted once per record instead of once per overlap,
 // which moves far fewer bytes than sorting the 64-bit keys directly.
 //
-// Onesweep (one kernel per 8-bit digit): each CTA claims the next partition
-// of 4096 keys from an atomic counter, ranks its keys per digit with warp
+// Onesweep (one kernel per digit): each CTA claims the next partition of 4096
+// keys from an atomic counter, ranks its keys per digit with warp
 // match/ballot, publishes per-digit counts and resolves its global offsets by
-// decoupled look-back over earlier partitions, then scatters through shared
-// memory so that global stores are contiguous per digit. Every spin-wait is
-// bounded: on expiry it raises GS_ERR_TIMEOUT in the workspace error word and
-// carries on with what it has.
+// decoupled look-back over earlier partitions (four predecessors per load
+// round), then scatters through shared memory so that global stores are
+// contiguous per digit. Every spin-wait is bounded: on expiry it raises
+// GS_ERR_TIMEOUT in the workspace error word and carries on with what it has.
 #include <algorithm>
 #include <utility>
 
@@ -40,16 +43,18 @@ constexpr int kSpinLimit = 1 << 20;
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems; // keys per partition
-constexpr int kCompactItems = 8;
-constexpr int kCompactTile = 256 * kCompactItems;
+constexpr int kCompactVec = 8;                       // uint4 loads per lane
+constexpr int kCompactTile = 256 * 4 * kCompactVec;  // 8192 records per partition
 constexpr int kEmitItems = 8;
-constexpr int kEmitTile = 256 * kEmitItems;
+constexpr int kEmitTile = 256 * kEmitItems;          // 2048 records per partition
+constexpr int kHistSlot = 512;                       // histogram entries per pass
+constexpr int kLookWindow = 4;
 
 enum Counter {
     CTR_COMPACT = 0,
-    CTR_DEPTH = 1,   // 4 passes
+    CTR_DEPTH = 1, // 4 passes
     CTR_EMIT = 5,
-    CTR_TILE = 6,    // up to 4 passes
+    CTR_TILE = 6,  // up to 3 passes
     CTR_COUNT = 10
 };
 
@@ -61,6 +66,37 @@ struct WsHeader {
     uint32_t ctr[CTR_COUNT];
     uint32_t pad[64 - 4 - CTR_COUNT];
 };
+
+// Digit plan of the tile-id sort.
+struct TilePlan {
+    int passes;
+    int bits[3];
+    int shift[3];
+};
+
+TilePlan tile_plan(int64_t total_tiles)
+{
+    int b = 1;
+    while (((int64_t)1 << b) < total_tiles) ++b;
+    TilePlan p{};
+    if (b <= 8) {
+        p.passes = 1; p.bits[0] = 8;
+    } else if (b <= 16) {
+        p.passes = 2; p.bits[0] = p.bits[1] = 8;
+    } else if (b <= 18) {
+        p.passes = 2; p.bits[0] = p.bits[1] = 9;
+    } else if (b <= 24) {
+        p.passes = 3; p.bits[0] = p.bits[1] = p.bits[2] = 8;
+    } else {
+        p.passes = 3; p.bits[0] = p.bits[1] = p.bits[2] = 9; // up to 2^27 tiles (< 2^30 checked)
+    }
+    int s = 0;
+    for (int i = 0; i < p.passes; ++i) {
+        p.shift[i] = s;
+        s += p.bits[i];
+    }
+    return p;
+}
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p)
 {
@@ -86,6 +122,17 @@ __device__ __forceinline__ uint32_t warp_sum(uint32_t v)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
 }
 
 __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b)
@@ -136,12 +183,7 @@ __device__ uint32_t lookback_scalar(uint32_t *state, uint32_t part, uint32_t agg
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp, uint32_t &total)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
+    const uint32_t x = warp_incl_scan(v);
     if (lane == 31) s_warp[warp] = x;
     __syncthreads();
     uint32_t wex = 0, tot = 0;
@@ -155,90 +197,118 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp
     return wex + x - v;
 }
 
-// 1. compaction of drawn records, index order preserved.
+// 1. compaction of drawn records, index order preserved, plus the histograms
+// of the four depth digits. Lane l of warp w holds records
+// base + 1024 w + 4 (32 j + l) + e, e < 4, j < kCompactVec (uint4 loads).
 __global__ void __launch_bounds__(256)
 compact_kernel(const uint32_t *__restrict__ tiles, const uint32_t *__restrict__ dkey, uint32_t N,
                uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, WsHeader *hdr,
-               uint32_t *state)
+               uint32_t *state, uint32_t *__restrict__ hist)
 {
     __shared__ uint32_t s_part, s_excl, s_warp[8];
+    __shared__ uint32_t s_h[4][256];
+    for (int i = threadIdx.x; i < 4 * 256; i += 256) (&s_h[0][0])[i] = 0;
     if (threadIdx.x == 0) s_part = atomicAdd(&hdr->ctr[CTR_COMPACT], 1u);
     __syncthreads();
     const uint32_t part = s_part;
     const uint32_t nparts = (N + kCompactTile - 1) / kCompactTile;
     if (part >= nparts) return;
-    const uint32_t base = part * kCompactTile + threadIdx.x * kCompactItems;
-    uint32_t flags = 0, cnt = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t wbase = part * kCompactTile + warp * (kCompactTile / 8);
+    uint32_t flags[kCompactVec], incl[kCompactVec], off[kCompactVec];
+    uint32_t running = 0;
 #pragma unroll
-    for (int j = 0; j < kCompactItems; ++j) {
-        const uint32_t idx = base + j;
-        const bool f = idx < N && tiles[idx] > 0;
-        flags |= (uint32_t)f << j;
-        cnt += f;
+    for (int j = 0; j < kCompactVec; ++j) {
+        const uint32_t e0 = wbase + 4 * (32 * j + lane);
+        uint32_t f = 0;
+        if (e0 + 3 < N) {
+            const uint4 t4 = reinterpret_cast<const uint4 *>(tiles)[e0 / 4];
+            f = (t4.x > 0) | (t4.y > 0) << 1 | (t4.z > 0) << 2 | (t4.w > 0) << 3;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (e0 + e < N && tiles[e0 + e] > 0) f |= 1u << e;
+        }
+        flags[j] = f;
+        const uint32_t x = warp_incl_scan(__popc(f));
+        incl[j] = x;
+        off[j] = running;
+        running += __shfl_sync(0xffffffffu, x, 31);
     }
-    uint32_t total;
-    const uint32_t excl_t = block_excl_scan(cnt, s_warp, total);
+    if (lane == 0) s_warp[warp] = running;
+    __syncthreads();
+    uint32_t warp_excl = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const uint32_t t = s_warp[w];
+        warp_excl += (w < warp) ? t : 0u;
+        total += t;
+    }
     if (threadIdx.x < 32) {
         const uint32_t e = lookback_scalar(state, part, total, &hdr->err);
         if (threadIdx.x == 0) s_excl = e;
     }
     __syncthreads();
-    uint32_t pos = s_excl + excl_t;
+    const uint32_t excl = s_excl;
 #pragma unroll
-    for (int j = 0; j < kCompactItems; ++j) {
-        if (flags >> j & 1u) {
-            if (pos < N) { // always true unless a look-back wait timed out
-                keys_out[pos] = dkey[base + j];
-                vals_out[pos] = base + j;
+    for (int j = 0; j < kCompactVec; ++j) {
+        uint32_t pos = excl + warp_excl + off[j] + incl[j] - __popc(flags[j]);
+        const uint32_t e0 = wbase + 4 * (32 * j + lane);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (flags[j] >> e & 1u) {
+                const uint32_t key = dkey[e0 + e];
+                if (pos < N) { // always true unless a look-back wait timed out
+                    keys_out[pos] = key;
+                    vals_out[pos] = e0 + e;
+                }
+                ++pos;
+#pragma unroll
+                for (int p = 0; p < 4; ++p) atomicAdd(&s_h[p][(key >> (8 * p)) & 255u], 1u);
             }
-            ++pos;
         }
     }
-    if (part == nparts - 1 && threadIdx.x == 255) hdr->n_vis = pos;
+    if (part == nparts - 1 && threadIdx.x == 0) hdr->n_vis = sat_add(excl, total);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * 256; i += 256) {
+        const uint32_t v = (&s_h[0][0])[i];
+        if (v) atomicAdd(&hist[(i >> 8) * kHistSlot + (i & 255)], v);
+    }
 }
 
-// Histograms of every digit position used by the passes of one sort.
-__global__ void __launch_bounds__(256)
-histogram_kernel(const uint32_t *__restrict__ keys, const uint32_t *n_ptr, int passes,
-                 uint32_t *__restrict__ hist)
+// One Onesweep pass over BITS bits starting at `shift`. Dynamic shared
+// memory: keys, values, per-warp digit counters, two per-digit tables.
+template <int BITS>
+constexpr size_t onesweep_smem()
 {
-    __shared__ uint32_t s_h[4][256];
-    for (int i = threadIdx.x; i < 4 * 256; i += 256) (&s_h[0][0])[i] = 0;
-    __syncthreads();
-    const uint32_t n = *n_ptr;
-    for (uint32_t i = blockIdx.x * 256 + threadIdx.x; i < n; i += gridDim.x * 256) {
-        const uint32_t k = keys[i];
-        for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p][(k >> (8 * p)) & 255u], 1u);
-    }
-    __syncthreads();
-    for (int p = 0; p < passes; ++p) {
-        const uint32_t v = s_h[p][threadIdx.x];
-        if (v) atomicAdd(&hist[p * 256 + threadIdx.x], v);
-    }
+    return sizeof(uint32_t) * (2 * kSortTile + 8 * (1 << BITS) + 2 * (1 << BITS) + 8 + 1);
 }
 
-// One Onesweep pass over 8 bits starting at `shift`.
-__global__ void __launch_bounds__(kSortThreads)
+template <int BITS>
+__global__ void __launch_bounds__(kSortThreads, 4) // 4 CTAs per SM: the pass is latency-bound
 onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                 uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
                 const uint32_t *n_ptr, int shift, const uint32_t *__restrict__ hist,
                 uint32_t *state, uint32_t *ctr, uint32_t *err)
 {
-    __shared__ uint32_t s_keys[kSortTile];
-    __shared__ uint32_t s_vals[kSortTile];
-    __shared__ uint32_t s_whist[8][256];
-    __shared__ uint32_t s_bexcl[256];
-    __shared__ uint32_t s_goff[256];
-    __shared__ uint32_t s_warp[8];
-    __shared__ uint32_t s_part;
+    constexpr int R = 1 << BITS;
+    constexpr uint32_t M = R - 1;
+    constexpr int DPT = R / kSortThreads; // digits per thread (consecutive)
+    extern __shared__ uint32_t smem[];
+    uint32_t *s_keys = smem;
+    uint32_t *s_vals = s_keys + kSortTile;
+    uint32_t *s_whist = s_vals + kSortTile; // [8][R]
+    uint32_t *s_bexcl = s_whist + 8 * R;
+    uint32_t *s_goff = s_bexcl + R;
+    uint32_t *s_warp = s_goff + R;
+    uint32_t *s_part = s_warp + 8;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_part = atomicAdd(ctr, 1u);
-#pragma unroll
-    for (int w = 0; w < 8; ++w) s_whist[w][tid] = 0;
+    if (tid == 0) *s_part = atomicAdd(ctr, 1u);
+    for (int i = tid; i < 8 * R; i += kSortThreads) s_whist[i] = 0;
     __syncthreads();
     const uint32_t n = *n_ptr;
-    const uint32_t part = s_part;
+    const uint32_t part = *s_part;
     const uint32_t nparts = (n + kSortTile - 1) / kSortTile;
     if (part >= nparts) return;
 
@@ -249,79 +319,106 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
     for (int j = 0; j < kSortItems; ++j) {
         const uint32_t idx = wbase + j * 32 + lane;
         const bool ok = idx < n;
-        k[j] = ok ? keys_in[idx] : 0xffffffffu; // invalid keys rank last (digit 255, highest index)
+        k[j] = ok ? keys_in[idx] : 0xffffffffu; // invalid keys rank last (top digit, highest index)
         v[j] = ok ? vals_in[idx] : 0u;
     }
     // rank within the warp: match lanes with equal digits
     const uint32_t lt = lanemask_lt();
+    uint32_t *wh = s_whist + warp * R;
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
-        const uint32_t d = (k[j] >> shift) & 255u;
+        const uint32_t d = (k[j] >> shift) & M;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const int leader = __ffs(peers) - 1;
         uint32_t old = 0;
         if (lane == leader) {
-            old = s_whist[warp][d];
-            s_whist[warp][d] = old + __popc(peers);
+            old = wh[d];
+            wh[d] = old + __popc(peers);
         }
         old = __shfl_sync(0xffffffffu, old, leader);
         r[j] = old + __popc(peers & lt);
         __syncwarp();
     }
     __syncthreads();
-    // per digit (thread = digit): warp-exclusive offsets and block count
-    uint32_t cnt = 0;
+    // per digit: warp-exclusive offsets and block counts
+    uint32_t cnt[DPT], csum = 0, hsum = 0, hv[DPT];
 #pragma unroll
-    for (int w = 0; w < 8; ++w) {
-        const uint32_t c = s_whist[w][tid];
-        s_whist[w][tid] = cnt;
-        cnt += c;
+    for (int q = 0; q < DPT; ++q) {
+        const int d = tid * DPT + q;
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const uint32_t x = s_whist[w * R + d];
+            s_whist[w * R + d] = c;
+            c += x;
+        }
+        cnt[q] = c;
+        csum += c;
+        hv[q] = hist[d];
+        hsum += hv[q];
     }
     uint32_t tot;
-    const uint32_t bex = block_excl_scan(cnt, s_warp, tot);
-    s_bexcl[tid] = bex;
-    // global digit offsets from the histogram (every CTA rescans 256 values)
+    uint32_t bex = block_excl_scan(csum, s_warp, tot);
     __syncthreads();
-    uint32_t htot;
-    const uint32_t hex = block_excl_scan(hist[tid], s_warp + 0, htot);
-    (void)htot;
-    // invalid keys exist only in the last partition, all with digit 255
+    uint32_t hex = block_excl_scan(hsum, s_warp, tot);
+    // invalid keys exist only in the last partition, all with the top digit
     const uint32_t last_valid = n - part * kSortTile;
     const uint32_t n_invalid = last_valid < (uint32_t)kSortTile ? kSortTile - last_valid : 0u;
-    const uint32_t agg = cnt - (tid == 255 ? n_invalid : 0u);
-    // decoupled look-back, one digit per thread
-    uint32_t *st = state + (size_t)part * 256;
-    uint32_t excl = 0;
-    if (part == 0) {
-        st_relaxed(&st[tid], kFlagIncl | agg);
-    } else {
-        st_relaxed(&st[tid], kFlagAgg | agg);
-        int64_t p = (int64_t)part - 1;
-        int spins = 0;
-        while (p >= 0) {
-            const uint32_t s = ld_relaxed(&state[(size_t)p * 256 + tid]);
-            const uint32_t f = s >> 30;
-            if (f == 0) {
-                if (++spins > kSpinLimit) {
-                    atomicOr(err, (uint32_t)GS_ERR_TIMEOUT);
-                    break;
+    uint32_t *st = state + (size_t)part * R;
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+        const int d = tid * DPT + q;
+        s_bexcl[d] = bex;
+        bex += cnt[q];
+        const uint32_t agg = cnt[q] - (d == (int)M ? n_invalid : 0u);
+        uint32_t excl = 0;
+        if (part == 0) {
+            st_relaxed(&st[d], kFlagIncl | agg);
+        } else {
+            st_relaxed(&st[d], kFlagAgg | agg);
+            // decoupled look-back, kLookWindow predecessors per load round
+            int64_t p = (int64_t)part - 1;
+            int spins = 0;
+            bool done = false;
+            while (!done && p >= 0) {
+                uint32_t s[kLookWindow];
+#pragma unroll
+                for (int w = 0; w < kLookWindow; ++w)
+                    s[w] = (p - w >= 0) ? ld_relaxed(&state[(size_t)(p - w) * R + d]) : kFlagIncl;
+                int used = 0;
+                bool stall = false;
+#pragma unroll
+                for (int w = 0; w < kLookWindow; ++w) {
+                    if (done || stall) continue;
+                    const uint32_t f = s[w] >> 30;
+                    if (f == 0) {
+                        stall = true;
+                        continue;
+                    }
+                    excl = sat_add(excl, s[w] & kValMask);
+                    ++used;
+                    if (f == 2) done = true;
                 }
-                __nanosleep(32);
-                continue;
+                p -= used;
+                if (stall && !done) {
+                    if (++spins > kSpinLimit) {
+                        atomicOr(err, (uint32_t)GS_ERR_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(32);
+                }
             }
-            excl = sat_add(excl, s & kValMask);
-            if (f == 2) break;
-            --p;
+            st_relaxed(&st[d], kFlagIncl | sat_add(excl, agg));
         }
-        st_relaxed(&st[tid], kFlagIncl | sat_add(excl, agg));
+        s_goff[d] = hex + excl;
+        hex += hv[q];
     }
-    s_goff[tid] = hex + excl;
     __syncthreads();
     // scatter into shared memory in digit order
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
-        const uint32_t d = (k[j] >> shift) & 255u;
-        const uint32_t lp = s_bexcl[d] + s_whist[warp][d] + r[j];
+        const uint32_t d = (k[j] >> shift) & M;
+        const uint32_t lp = s_bexcl[d] + wh[d] + r[j];
         s_keys[lp] = k[j];
         s_vals[lp] = v[j];
     }
@@ -329,7 +426,7 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
     const uint32_t nvalid = min(last_valid, (uint32_t)kSortTile);
     for (uint32_t i = tid; i < nvalid; i += kSortThreads) {
         const uint32_t key = s_keys[i];
-        const uint32_t d = (key >> shift) & 255u;
+        const uint32_t d = (key >> shift) & M;
         const uint32_t o = s_goff[d] + i - s_bexcl[d];
         if (o < n) { // always true unless a look-back wait timed out
             keys_out[o] = key;
@@ -338,15 +435,17 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
     }
 }
 
-// 3. overlap emission in depth order.
+// 3. overlap emission in depth order, plus the tile-digit histograms.
 __global__ void __launch_bounds__(256)
 emit_kernel(const __grid_constant__ CamTable cams, int P, uint32_t n_records,
             const uint32_t *__restrict__ sorted_vals,
             const uint32_t *__restrict__ tiles, const ushort4 *__restrict__ rects,
             uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, uint32_t capacity,
-            WsHeader *hdr, uint32_t *state)
+            WsHeader *hdr, uint32_t *state, TilePlan plan, uint32_t *__restrict__ hist)
 {
     __shared__ uint32_t s_part, s_excl, s_warp[8];
+    __shared__ uint32_t s_h[3][kHistSlot];
+    for (int i = threadIdx.x; i < 3 * kHistSlot; i += 256) (&s_h[0][0])[i] = 0;
     if (threadIdx.x == 0) s_part = atomicAdd(&hdr->ctr[CTR_EMIT], 1u);
     __syncthreads();
     const uint32_t nv = hdr->n_vis;
@@ -368,12 +467,7 @@ emit_kernel(const __grid_constant__ CamTable cams, int P, uint32_t n_records,
         v[j] = vv;
         cnt[j] = valid ? tiles[vv] : 0u;
         rc[j] = valid ? rects[vv] : make_ushort4(0, 0, 0, 0);
-        uint32_t x = cnt[j];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
+        const uint32_t x = warp_incl_scan(cnt[j]);
         incl[j] = x;
         off[j] = running;
         running += __shfl_sync(0xffffffffu, x, 31);
@@ -423,8 +517,11 @@ emit_kernel(const __grid_constant__ CamTable cams, int P, uint32_t n_records,
             const uint32_t row = l / erw, col = l - row * erw;
             const uint32_t o = out_base + p;
             if (p < w_total && o < capacity) {
-                keys_out[o] = etb + row * etx + col;
+                const uint32_t key = etb + row * etx + col;
+                keys_out[o] = key;
                 vals_out[o] = ev;
+                for (int q = 0; q < plan.passes; ++q)
+                    atomicAdd(&s_h[q][(key >> plan.shift[q]) & ((1u << plan.bits[q]) - 1u)], 1u);
             }
         }
     }
@@ -433,6 +530,11 @@ emit_kernel(const __grid_constant__ CamTable cams, int P, uint32_t n_records,
         hdr->n_over_raw = tot;
         hdr->n_over = min(tot, capacity);
         if (tot > capacity || tot >= kValMask) atomicOr(&hdr->err, (uint32_t)GS_ERR_CAPACITY);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < plan.passes * kHistSlot; i += 256) {
+        const uint32_t x = (&s_h[0][0])[i];
+        if (x) atomicAdd(&hist[i], x);
     }
 }
 
@@ -459,23 +561,27 @@ struct WsLayout {
     size_t hdr, hist, st_compact, st_depth, st_emit, st_tile, zero_end;
     size_t dk0, dk1, dv0, dv1, tk0, tk1, tv1, total;
     uint32_t parts_depth, parts_tile;
+    size_t st_depth_stride, st_tile_stride; // uint32 entries per pass
 };
 
-WsLayout ws_layout(int64_t N, int64_t cap)
+WsLayout ws_layout(int64_t N, int64_t cap, const TilePlan &plan)
 {
     WsLayout L;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o += align256(bytes); return r; };
     L.parts_depth = (uint32_t)((N + kSortTile - 1) / kSortTile);
     L.parts_tile = (uint32_t)((cap + kSortTile - 1) / kSortTile);
+    const int rt = 1 << plan.bits[0];
+    L.st_depth_stride = (size_t)256 * (L.parts_depth + 1);
+    L.st_tile_stride = (size_t)rt * (L.parts_tile + 1);
     L.hdr = take(sizeof(WsHeader));
-    L.hist = take(sizeof(uint32_t) * 8 * 256);
+    L.hist = take(sizeof(uint32_t) * 8 * kHistSlot);
     L.st_compact = take(sizeof(uint32_t) * ((N + kCompactTile - 1) / kCompactTile + 1));
-    L.st_depth = take(sizeof(uint32_t) * 4 * 256 * (size_t)(L.parts_depth + 1));
+    L.st_depth = take(sizeof(uint32_t) * 4 * L.st_depth_stride);
     L.st_emit = take(sizeof(uint32_t) * ((N + kEmitTile - 1) / kEmitTile + 1));
-    L.st_tile = take(sizeof(uint32_t) * 4 * 256 * (size_t)(L.parts_tile + 1));
+    L.st_tile = take(sizeof(uint32_t) * plan.passes * L.st_tile_stride);
     L.zero_end = o;
-    L.dk0 = take(sizeof(uint32_t) * N);
+    L.dk0 = take(sizeof(uint32_t) * N + 16);
     L.dk1 = take(sizeof(uint32_t) * N);
     L.dv0 = take(sizeof(uint32_t) * N);
     L.dv1 = take(sizeof(uint32_t) * N);
@@ -486,11 +592,19 @@ WsLayout ws_layout(int64_t N, int64_t cap)
     return L;
 }
 
-int tile_bits(int64_t total_tiles)
+template <int BITS>
+cudaError_t launch_onesweep(unsigned grid, cudaStream_t s, const uint32_t *ki, const uint32_t *vi,
+                            uint32_t *ko, uint32_t *vo, const uint32_t *n, int shift,
+                            const uint32_t *hist, uint32_t *state, uint32_t *ctr, uint32_t *err)
 {
-    int b = 1;
-    while (((int64_t)1 << b) < total_tiles) ++b;
-    return b;
+    const size_t sm = onesweep_smem<BITS>();
+    cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<BITS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    onesweep_kernel<BITS><<<grid ? grid : 1, kSortThreads, sm, s>>>(ki, vi, ko, vo, n, shift, hist,
+                                                                   state, ctr, err);
+    count_launch();
+    return cudaPeekAtLastError();
 }
 
 } // namespace
@@ -500,9 +614,8 @@ using namespace gs;
 
 extern "C" size_t gs_bin_sort_workspace_bytes(int64_t n_records, int64_t capacity, int64_t total_tiles)
 {
-    (void)total_tiles;
-    if (n_records < 0 || capacity < 0) return 0;
-    return ws_layout(n_records, capacity).total;
+    if (n_records < 0 || capacity < 0 || total_tiles < 0) return 0;
+    return ws_layout(n_records, capacity, tile_plan(total_tiles)).total;
 }
 
 extern "C" gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t ncam, int32_t P,
@@ -518,7 +631,8 @@ extern "C" gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t nc
     if (N > 0 && (!d_splat2d || ((uintptr_t)d_splat2d & 255))) return GS_ERR_ARG;
     CamTable t;
     if (!build_cam_table(cams, ncam, cfg, &t)) return GS_ERR_ARG;
-    const WsLayout L = ws_layout(N, capacity);
+    const TilePlan plan = tile_plan(t.total_tiles);
+    const WsLayout L = ws_layout(N, capacity, plan);
     if (workspace_bytes < L.total) return GS_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char *ws = static_cast<char *>(d_workspace);
@@ -531,49 +645,51 @@ extern "C" gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t nc
         return GS_ERR_CUDA;
     if (N > 0) {
         Splat2DConst sp = splat2d_const(d_splat2d, N);
-        // 1. compaction
+        // 1. compaction + depth-digit histograms
         compact_kernel<<<(unsigned)((N + kCompactTile - 1) / kCompactTile), 256, 0, s>>>(
-            sp.tiles, sp.dkey, (uint32_t)N, U(L.dk0), U(L.dv0), hdr, U(L.st_compact));
+            sp.tiles, sp.dkey, (uint32_t)N, U(L.dk0), U(L.dv0), hdr, U(L.st_compact), hist);
         count_launch();
         GS_LAUNCH_CHECK();
         // 2. depth sort, 4 passes ping-pong: result back in (dk0, dv0)
-        const int hist_blocks = 148 * 4;
-        histogram_kernel<<<hist_blocks, 256, 0, s>>>(U(L.dk0), &hdr->n_vis, 4, hist);
-        count_launch();
-        GS_LAUNCH_CHECK();
         uint32_t *kin = U(L.dk0), *vin = U(L.dv0), *kout = U(L.dk1), *vout = U(L.dv1);
         for (int p = 0; p < 4; ++p) {
-            onesweep_kernel<<<L.parts_depth ? L.parts_depth : 1, kSortThreads, 0, s>>>(
-                kin, vin, kout, vout, &hdr->n_vis, 8 * p, hist + 256 * p,
-                U(L.st_depth) + (size_t)p * 256 * (L.parts_depth + 1), &hdr->ctr[CTR_DEPTH + p],
-                &hdr->err);
-            count_launch();
-            GS_LAUNCH_CHECK();
+            if (launch_onesweep<8>(L.parts_depth, s, kin, vin, kout, vout, &hdr->n_vis, 8 * p,
+                                   hist + kHistSlot * p, U(L.st_depth) + p * L.st_depth_stride,
+                                   &hdr->ctr[CTR_DEPTH + p], &hdr->err) != cudaSuccess) {
+                cudaGetLastError();
+                return GS_ERR_CUDA;
+            }
             std::swap(kin, kout);
             std::swap(vin, vout);
         }
         if (capacity > 0) {
             // 3. emission into the buffers that make the last tile pass land in d_vals
-            const int tb = tile_bits(t.total_tiles);
-            const int passes = (tb + 7) / 8;
             uint32_t *ek = U(L.tk0);
-            uint32_t *ev = (passes % 2 == 0) ? d_vals : U(L.tv1);
+            uint32_t *ev = (plan.passes % 2 == 0) ? d_vals : U(L.tv1);
+            uint32_t *thist = hist + 4 * kHistSlot;
             emit_kernel<<<(unsigned)((N + kEmitTile - 1) / kEmitTile), 256, 0, s>>>(
-                t, P, (uint32_t)N, vin, sp.tiles, sp.rect, ek, ev, (uint32_t)capacity, hdr, U(L.st_emit));
+                t, P, (uint32_t)N, vin, sp.tiles, sp.rect, ek, ev, (uint32_t)capacity, hdr,
+                U(L.st_emit), plan, thist);
             count_launch();
             GS_LAUNCH_CHECK();
             // 4. tile sort
-            histogram_kernel<<<hist_blocks, 256, 0, s>>>(ek, &hdr->n_over, passes, hist + 4 * 256);
-            count_launch();
-            GS_LAUNCH_CHECK();
             uint32_t *tki = ek, *tvi = ev, *tko = U(L.tk1), *tvo = (ev == d_vals) ? U(L.tv1) : d_vals;
-            for (int p = 0; p < passes; ++p) {
-                onesweep_kernel<<<L.parts_tile ? L.parts_tile : 1, kSortThreads, 0, s>>>(
-                    tki, tvi, tko, tvo, &hdr->n_over, 8 * p, hist + 256 * (4 + p),
-                    U(L.st_tile) + (size_t)p * 256 * (L.parts_tile + 1), &hdr->ctr[CTR_TILE + p],
-                    &hdr->err);
-                count_launch();
-                GS_LAUNCH_CHECK();
+            for (int p = 0; p < plan.passes; ++p) {
+                cudaError_t e;
+                if (plan.bits[p] == 9)
+                    e = launch_onesweep<9>(L.parts_tile, s, tki, tvi, tko, tvo, &hdr->n_over,
+                                           plan.shift[p], thist + kHistSlot * p,
+                                           U(L.st_tile) + p * L.st_tile_stride,
+                                           &hdr->ctr[CTR_TILE + p], &hdr->err);
+                else
+                    e = launch_onesweep<8>(L.parts_tile, s, tki, tvi, tko, tvo, &hdr->n_over,
+                                           plan.shift[p], thist + kHistSlot * p,
+                                           U(L.st_tile) + p * L.st_tile_stride,
+                                           &hdr->ctr[CTR_TILE + p], &hdr->err);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    return GS_ERR_CUDA;
+                }
                 std::swap(tki, tko);
                 std::swap(tvi, tvo);
             }

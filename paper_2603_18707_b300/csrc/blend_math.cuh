@@ -1,0 +1,81 @@
+// blend_math.cuh — per-(splat, tile) coefficients and the alpha evaluation
+// shared by the forward blend and its reverse pass, so that both take every
+// skip / clamp / stop decision with bit-identical arithmetic.
+//
+// The quadric of Eq. 1, Q = A dx^2 + 2 B dx dy + C dy^2 (dx, dy: pixel centre
+// minus mu'), is rewritten once per staged entry as a sum of two squares of
+// affine functions of the tile-local pixel coordinates (x, y):
+//   u = ux x + uy y + u0,  v = vy y + v0,  Q = u^2 + v^2,
+//   ux = sqrt(A), uy = B / sqrt(A), vy = sqrt((A C - B^2) / A)
+// (completing the square; A > 0 for the inverse of a covariance). A thread
+// then needs 2 FMAs per row and 2 per pixel for Q. Opacity is folded into the
+// kernel coefficients: o' f(Q) = p0 + p1 Q + p2 Q^2 + p3 Q^3 with p_i = o' c_i,
+// and o' exp(-Q/2) = 2^(p0 + p1 Q) with p0 = log2 o', p1 = -log2(e)/2.
+#pragma once
+
+#include "gs_common.cuh"
+
+namespace gs {
+
+struct BlendCoef {
+    float4 a; // ux, uy, u0, vy
+    float4 b; // v0, p0, p1, p2
+    float4 c; // red, green, blue, p3
+};
+
+// rec0 = (mu'x, mu'y, o', depth), rec1 = (A, B, C, x_cut), rec2 = (r, g, b, rho);
+// (ox, oy): pixel coordinates of the tile's corner.
+template <int KIND>
+__device__ __forceinline__ BlendCoef make_coef(const CfgDev &cfg, float4 r0, float4 r1, float4 r2,
+                                               float ox, float oy)
+{
+    const float mx = r0.x - ox, my = r0.y - oy, o = r0.z;
+    const float A = r1.x, B = r1.y, C = r1.z;
+    const float sA = sqrtf(A);
+    const float ux = sA, uy = B / sA;
+    const float vy = sqrtf(fmaxf(C - B * uy / sA, 0.f));
+    BlendCoef k;
+    k.a = make_float4(ux, uy, -fmaf(ux, mx, uy * my), vy);
+    float p0, p1, p2 = 0.f, p3 = 0.f;
+    if (KIND == GS_K_EXP) {
+        p0 = log2f(o);
+        p1 = -0.72134752044448170f; // -log2(e) / 2
+    } else {
+        p0 = o * cfg.c[0];
+        p1 = o * cfg.c[1];
+        p2 = o * cfg.c[2];
+        p3 = o * cfg.c[3];
+    }
+    k.b = make_float4(-vy * my, p0, p1, p2);
+    k.c = make_float4(r2.x, r2.y, r2.z, p3);
+    return k;
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// o' k(Q) before the alpha_max clamp.
+template <int KIND>
+__device__ __forceinline__ float alpha_of_q(const CfgDev &cfg, const float4 &b, float p3, float Q)
+{
+    if (KIND == GS_K_EXP) return ex2_approx(fmaf(b.z, Q, b.y));
+    if (KIND == GS_K_POLY1) return fmaf(b.z, Q, b.y);
+    if (KIND == GS_K_POLY2) return Q < cfg.x0 ? fmaf(fmaf(b.w, Q, b.z), Q, b.y) : 0.f;
+    return fmaf(fmaf(fmaf(p3, Q, b.w), Q, b.z), Q, b.y);
+}
+
+// dk/dQ of the kernel (without the opacity), for the reverse pass.
+template <int KIND>
+__device__ __forceinline__ float kernel_slope(const CfgDev &cfg, float Q, float alpha_raw, float o)
+{
+    if (KIND == GS_K_EXP) return -0.5f * alpha_raw / o;
+    if (KIND == GS_K_POLY1) return cfg.c[1];
+    if (KIND == GS_K_POLY2) return fmaf(2.f * cfg.c[2], Q, cfg.c[1]);
+    return fmaf(fmaf(3.f * cfg.c[3], Q, 2.f * cfg.c[2]), Q, cfg.c[1]);
+}
+
+} // namespace gs

@@ -207,12 +207,16 @@ preprocess_kernel(const __grid_constant__ CamTable cams, const __grid_constant__
                 }
             }
         }
-        out.rec[3 * n + 0] = r0;
-        out.rec[3 * n + 1] = r1;
-        out.rec[3 * n + 2] = r2;
-        out.rect[n] = rect;
+        // a record that covers no tile is never read past its tile count:
+        // only that count is written for it
         out.tiles[n] = ntiles;
-        out.dkey[n] = ntiles ? __float_as_uint(tz) : 0xffffffffu;
+        if (ntiles) {
+            out.rec[3 * n + 0] = r0;
+            out.rec[3 * n + 1] = r1;
+            out.rec[3 * n + 2] = r2;
+            out.rect[n] = rect;
+            out.dkey[n] = __float_as_uint(tz);
+        }
     }
 }
 

@@ -108,12 +108,13 @@ def test_binning_bit_exact(gs, case):
 
 @pytest.mark.parametrize("kind", ["exp", "poly1", "poly2", "poly3"])
 @pytest.mark.parametrize("cull", ["universal", "opacity"])
-def test_image_matches_oracle(gs, orc, small, kind, cull):
+@pytest.mark.parametrize("ppt", [1, 4])
+def test_image_matches_oracle(gs, orc, small, kind, cull, ppt):
     """Config-1 scene (4096 splats, 128^2): GPU image vs the untiled, unculled
     FP64 oracle within 2e-4 per channel outside threshold flips."""
     from paper_2603_18707_b300 import synth
     cam = synth.camera_small()
-    R = _gpu(gs, small, [cam], kind, cull)
+    R = _gpu(gs, small, [cam], kind, cull, px_per_thread=ppt)
     img = R.images()[0].cpu().numpy()
     T = R.per_camera(R.final_T)[0].cpu().numpy()
     oc = orc.camera_from_dict(cam)
@@ -155,8 +156,9 @@ def test_tile_shapes_identical_pixels(gs, orc, small):
     images for 8x8, 16x16 and 32x8 tiles on a ragged 100x75 frame."""
     from paper_2603_18707_b300 import synth
     cam = synth.camera_small(100, 75)
-    imgs = [_gpu(gs, small, [cam], "poly1", "opacity", tile=t).images()[0].cpu().numpy()
-            for t in ((16, 16), (8, 8), (32, 8), (8, 16))]
+    imgs = [_gpu(gs, small, [cam], "poly1", "opacity", tile=t, px_per_thread=p).images()[0].cpu().numpy()
+            for t, p in (((16, 16), 1), ((8, 8), 1), ((32, 8), 1), ((8, 16), 1), ((16, 16), 2),
+                         ((16, 16), 4), ((32, 8), 4), ((8, 8), 2))]
     for im in imgs[1:]:
         assert np.array_equal(im, imgs[0])
     sc = orc.activate(small)
