@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--height", type=int, default=1080)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-diff", action="store_true", help="skip the differentiable-render leg")
+    p.add_argument("--no-batched", action="store_true", help="skip the 64-camera batched leg")
     p.add_argument("--ppt", type=int, default=None, help="pixels per blend thread (1, 2, 4)")
     p.add_argument("--tile", type=str, default=None, help="tile shape WxH, e.g. 16x16")
     p.add_argument("--profile", choices=["poly1", "exp", "poly2", "poly3"], default=None,
@@ -335,6 +337,15 @@ def run_ours(a, world, rank, local):
                 "peak_source": "148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz (derived)",
                 "dominant_stage": dom}
 
+    extra = {}
+    if not a.no_diff:
+        del R, sc
+        torch.cuda.empty_cache()
+        extra["differentiable"] = bench_differentiable(a)
+    if not a.no_batched:
+        torch.cuda.empty_cache()
+        extra["batched"] = bench_batched(a)
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         import oracle
@@ -358,7 +369,93 @@ def run_ours(a, world, rank, local):
             "evals_per_step": evals, "overlaps_per_step": overlaps, "stages_ms": stages,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches}
+    line.update(extra)
     print(json.dumps(line), flush=True)
+
+
+def _events_ms(fn, steps):
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def bench_differentiable(a):
+    """1M-splat cluster scene, SH degree 3, one 1024x1024 camera, f1 with
+    opacity culling: forward + L1 loss against the render of a perturbed
+    copy + backward through torch.autograd.Function (gradients of means,
+    log-scales, quaternions, opacity logits and SH)."""
+    import torch
+
+    from paper_2603_18707_b300 import api, autograd, render, synth
+    P = 1_000_000
+    raw = synth.scene_clusters(P, 0, sh_degree=3)
+    cam = synth.orbit_cameras(1, 1024, 1024)[0]
+    cfg = api.make_config("poly1", "opacity")
+    Rt = render.Rasterizer([cam], cfg, P)
+    target = Rt.forward(render.activate(synth.perturbed(raw, 1))).clone()
+    del Rt
+    t = {k: torch.tensor(raw[k], device="cuda", requires_grad=True)
+         for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+    R = render.Rasterizer([cam], cfg, P)
+
+    def step():
+        for v in t.values():
+            v.grad = None
+        img = autograd.render(t["means"], t["log_scales"], t["quats"], t["opacity_logits"], t["sh"], 3, R)
+        (img - target).abs().mean().backward()
+
+    for _ in range(3):
+        step()
+    ms = _events_ms(step, max(5, a.steps // 6))
+    with torch.no_grad():
+        ms_fwd = _events_ms(lambda: autograd.render(t["means"], t["log_scales"], t["quats"],
+                                                    t["opacity_logits"], t["sh"], 3, R), 5)
+    return {"workload": "1M-splat cluster scene, SH degree 3, 1024x1024, f1 + opacity cull, L1 loss",
+            "ms_forward_backward": ms, "ms_forward": ms_fwd, "steps_per_s": 1e3 / ms,
+            "note": "forward includes the overlap-count read-back of Rasterizer.forward"}
+
+
+def bench_batched(a):
+    """Serving-style batch: 6M-splat cluster scene, SH degree 3, 64 cameras
+    of 640x360 / 1280x720 / 1920x1080 / 3840x2160 in a 4:3:2:1 mix, rendered
+    by one pass of the path with the blend as one persistent launch, the whole
+    pass captured in a CUDA graph and replayed. Launch shape from the
+    autotuner."""
+    import torch
+
+    from paper_2603_18707_b300 import api, autotune, render, synth
+    P = 6_000_000
+    raw = synth.scene_clusters(P, 0, sh_degree=3)
+    cams = synth.mixed_cameras(64)
+    sc = render.activate(raw)
+    npix = sum(c["width"] * c["height"] for c in cams)
+    out = {"workload": "6M-splat cluster scene, SH degree 3, 64 cameras 4:3:2:1 of "
+                       "640x360/1280x720/1920x1080/3840x2160", "megapixels": npix / 1e6}
+    for kind in ("poly1", "exp"):
+        tuned = autotune.autotune(cams, kind, "opacity", sc, P, persistent=True, steps=3, cache=None)
+        cfg = api.make_config(kind, "opacity", **autotune.config_overrides(tuned))
+        R = render.Rasterizer(cams, cfg, P, persistent=True)
+        R.forward(sc, n_eval=True)
+        evals = int(R.n_eval.to(torch.int64).sum().item())
+        graph = R.capture(sc)
+        for _ in range(3):
+            graph.replay()
+        ms = _events_ms(graph.replay, max(5, a.steps // 6))
+        ms_eager = _events_ms(lambda: R.run_async(sc), 3)
+        out[kind] = {"frames_per_s": 64 / (ms / 1e3), "ms_per_batch": ms, "ms_per_batch_eager": ms_eager,
+                     "gsplat_evals_per_s": evals / (ms / 1e3) / 1e9, "overlaps": R.n_records()[1],
+                     "autotuned": {"tile": tuned["tile"], "batch": tuned["batch"],
+                                   "px_per_thread": tuned["px_per_thread"]}}
+        del graph, R
+        torch.cuda.empty_cache()
+    out["speedup_poly1_vs_exp"] = out["exp"]["ms_per_batch"] / out["poly1"]["ms_per_batch"]
+    return out
 
 
 def main():

@@ -176,11 +176,20 @@ gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t ncam, int32_t
  *                contributing entry, 0 if none (may be NULL; the backward
  *                pass needs it)
  *   d_n_eval:    uint32 [sum_c H_c W_c] list entries evaluated (may be NULL)
- *   bg:          host float[3] background colour */
+ *   bg:          host float[3] background colour
+ *   d_work:      NULL for one CTA per tile; otherwise gs_render_work_bytes()
+ *                bytes of device memory (4-byte aligned) and the blend runs as
+ *                one persistent launch: a grid that fills every SM once, each
+ *                CTA taking the next tile of any camera from a counter in
+ *                d_work (reset by the call, on the stream).
+ * Pixel values do not depend on px_per_thread, batch or the launch mode; the
+ * tile shape changes only FP32 rounding (the per-tile coefficients are taken
+ * relative to the tile's corner). */
+size_t gs_render_work_bytes(void);
 gs_status gs_render(void *stream, const gs_camera *cams, int32_t ncam, int32_t P,
                     const gs_config *cfg, const void *d_splat2d, const uint32_t *d_vals,
                     const uint32_t *d_ranges, const float *bg, float *d_out_rgb,
-                    float *d_final_T, uint32_t *d_last, uint32_t *d_n_eval);
+                    float *d_final_T, uint32_t *d_last, uint32_t *d_n_eval, void *d_work);
 
 /* Reverse pass of gs_render and gs_preprocess for one or more cameras:
  * gradients of a loss L with respect to the splat inputs, given

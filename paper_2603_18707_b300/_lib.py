@@ -56,8 +56,9 @@ _SIGS = {
                            _vp, _sz, _vp, _vp, _vp, _vp]),
     "gs_bin_sort_noalloc": (_i32, [_vp, C.POINTER(GsCamera), _i32, _i32, C.POINTER(GsConfig), _vp,
                                    _i64, _vp, _vp, _vp, _vp]),
+    "gs_render_work_bytes": (_sz, []),
     "gs_render": (_i32, [_vp, C.POINTER(GsCamera), _i32, _i32, C.POINTER(GsConfig), _vp, _vp, _vp,
-                         C.POINTER(C.c_float), _vp, _vp, _vp, _vp]),
+                         C.POINTER(C.c_float), _vp, _vp, _vp, _vp, _vp]),
     "gs_grad2d_bytes": (_sz, [_i32, _i32]),
     "gs_render_backward": (_i32, [_vp, C.POINTER(GsCamera), _i32, _i32, C.POINTER(GsConfig),
                                   _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp,

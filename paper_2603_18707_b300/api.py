@@ -127,13 +127,19 @@ def gs_bin_sort_noalloc(cams, P, cfg, splat2d, capacity, vals, ranges, keys64=No
         _p(vals), _p(ranges), _p(keys64), _p(count)))
 
 
+def gs_render_work_bytes() -> int:
+    return int(lib().gs_render_work_bytes())
+
+
 def gs_render(cams, P, cfg, splat2d, vals, ranges, bg, out_rgb, final_T=None, last=None,
-              n_eval=None, stream=None):
+              n_eval=None, work=None, stream=None):
+    """work: None (one CTA per tile) or a device buffer of
+    gs_render_work_bytes() bytes (one persistent launch)."""
     arr = camera_array(cams)
     bgc = (C.c_float * 3)(*[float(v) for v in bg])
     check("gs_render", lib().gs_render(
         _stream(stream), arr, len(arr), int(P), C.byref(cfg), _p(splat2d), _p(vals), _p(ranges),
-        bgc, _f32(out_rgb), _f32(final_T), _p(last), _p(n_eval)))
+        bgc, _f32(out_rgb), _f32(final_T), _p(last), _p(n_eval), _p(work)))
 
 
 def gs_render_backward(cams, P, cfg, means, scales, quats, opacities, sh, sh_degree, splat2d, vals,

@@ -598,9 +598,17 @@ cudaError_t launch_onesweep(unsigned grid, cudaStream_t s, const uint32_t *ki, c
                             const uint32_t *hist, uint32_t *state, uint32_t *ctr, uint32_t *err)
 {
     const size_t sm = onesweep_smem<BITS>();
-    cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<BITS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
+    // the shared-memory opt-in is set once per device (so that later calls,
+    // e.g. under stream capture, only launch)
+    static bool attr_set[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cudaGetLastError();
+    if (dev >= 64 || !attr_set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<BITS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        if (dev < 64) attr_set[dev] = true;
+    }
     onesweep_kernel<BITS><<<grid ? grid : 1, kSortThreads, sm, s>>>(ki, vi, ko, vo, n, shift, hist,
                                                                    state, ctr, err);
     count_launch();

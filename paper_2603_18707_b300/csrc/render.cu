@@ -1,38 +1,50 @@
 // render.cu — front-to-back blending per tile (sm_103a).
 //
-// One CTA per (camera, tile). Each thread owns PPT horizontally adjacent
-// pixels of one row. The tile's depth-sorted list is streamed through shared
-// memory in batches: the block gathers the batch's 48-byte records and turns
-// each into the per-tile coefficients of blend_math.cuh (two affine forms
-// whose squares sum to the quadric, opacity folded into the kernel). Then every
-// thread walks the batch. Per entry and pixel (Sec. 2, Eq. 1 / 2 / 6):
+// One CTA renders one (camera, tile) at a time. Each thread owns PPT
+// horizontally adjacent pixels of one row. The tile's depth-sorted list is
+// streamed through shared memory in batches of `batch` entries: the block
+// gathers the batch's 48-byte records and turns each into the per-tile
+// coefficients of blend_math.cuh (two affine forms whose squares sum to the
+// quadric, opacity folded into the kernel). Then every thread walks the
+// batch. Per entry and pixel (Sec. 2, Eq. 1 / 2 / 6):
 //   Q = u^2 + v^2,  alpha = min(alpha_max, o' k(Q)),
 //   skip if alpha < eps; stop (without adding) if T (1 - alpha) < t_min;
 //   C += c alpha T; T *= 1 - alpha.
 // Cost per entry and thread: 2 LDS.128, 3 FP32 ops per row and 3 per pixel
 // for alpha (f1), the blend FMAs only where alpha >= eps. The polynomial
-// kernels use FMAs only; exp adds one MUFU ex2. The block leaves its list as
+// kernels use FMAs only; exp adds one MUFU ex2. The block leaves a list as
 // soon as every pixel has stopped (__syncthreads_count at each batch). The
 // kernel is bound by instruction issue on the FP32 pipes.
+//
+// Launch modes: one CTA per tile (grid = all tiles of all cameras), or
+// persistent: a grid sized to fill every SM once, each CTA taking the next
+// tile from an atomic counter until all tiles of all cameras are done (one
+// launch for any mix of resolutions, balanced dynamically).
+#include <algorithm>
+
 #include "blend_math.cuh"
 
 namespace gs {
 namespace {
 
-constexpr int kBatch = 256;
+constexpr int kMaxBatch = 256;
+
+struct RenderArgs {
+    const float4 *rec;
+    const uint32_t *vals;
+    const uint2 *ranges;
+    uint32_t n_records;
+    float bg0, bg1, bg2;
+    float *out;
+    float *final_T;
+    uint32_t *last;
+    uint32_t *n_eval;
+};
 
 template <int KIND, int PPT>
-__global__ void __launch_bounds__(256 / PPT)
-render_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
-              const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
-              const uint2 *__restrict__ ranges, uint32_t n_records, float bg0, float bg1, float bg2,
-              float *__restrict__ out, float *__restrict__ final_T, uint32_t *__restrict__ last,
-              uint32_t *__restrict__ n_eval)
+__device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &cfg, const RenderArgs &g,
+                                            int gtile, float4 *s_a, float4 *s_b, float4 *s_c)
 {
-    __shared__ float4 s_a[kBatch];
-    __shared__ float4 s_b[kBatch];
-    __shared__ float4 s_c[kBatch];
-    const int gtile = blockIdx.x;
     int c = 0;
     while (c + 1 < cams.ncam && cams.cam[c + 1].tile_base <= gtile) ++c;
     const CamDev &cm = cams.cam[c];
@@ -43,9 +55,10 @@ render_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ Cfg
     const float ox = (float)(tx * cfg.tile_w), oy = (float)(ty * cfg.tile_h);
     const int px0 = tx * cfg.tile_w + lx, py = ty * cfg.tile_h + ly;
     const float y = ly + 0.5f;
-    const uint2 rg = ranges[gtile];
+    const uint2 rg = g.ranges[gtile];
     const uint32_t n = rg.y - rg.x;
     const int nthreads = blockDim.x;
+    const int B = cfg.batch;
 
     float T[PPT], C0[PPT], C1[PPT], C2[PPT], xs[PPT];
     uint32_t lastc[PPT], ne[PPT];
@@ -60,21 +73,21 @@ render_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ Cfg
         if (px0 + k < cm.W && py < cm.H) active |= 1u << k;
     }
     const float eps = cfg.eps, amax = cfg.alpha_max, tmin = cfg.t_min;
-    for (uint32_t base = 0; base < n; base += kBatch) {
+    for (uint32_t base = 0; base < n; base += B) {
         if (__syncthreads_count(active != 0) == 0) break;
-        for (int i = threadIdx.x; i < kBatch; i += nthreads) {
+        for (int i = threadIdx.x; i < B; i += nthreads) {
             if (base + i < n) {
-                uint32_t v = vals[rg.x + base + i];
-                if (v >= n_records) v = 0; // only after a timed-out sort wait
-                const BlendCoef k = make_coef<KIND>(cfg, rec[3 * (size_t)v + 0], rec[3 * (size_t)v + 1],
-                                                    rec[3 * (size_t)v + 2], ox, oy);
+                uint32_t v = g.vals[rg.x + base + i];
+                if (v >= g.n_records) v = 0; // only after a timed-out sort wait
+                const BlendCoef k = make_coef<KIND>(cfg, g.rec[3 * (size_t)v + 0], g.rec[3 * (size_t)v + 1],
+                                                    g.rec[3 * (size_t)v + 2], ox, oy);
                 s_a[i] = k.a;
                 s_b[i] = k.b;
                 s_c[i] = k.c;
             }
         }
         __syncthreads();
-        const int cnt = (int)min((uint32_t)kBatch, n - base);
+        const int cnt = (int)min((uint32_t)B, n - base);
         for (int j = 0; j < cnt && active; ++j) {
             const float4 a = s_a[j];
             const float4 b = s_b[j];
@@ -116,27 +129,74 @@ render_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ Cfg
     for (int k = 0; k < PPT; ++k) {
         if (px0 + k < cm.W && py < cm.H) {
             const int64_t pix = cm.pix_base + (int64_t)py * cm.W + px0 + k;
-            out[3 * pix + 0] = fmaf(T[k], bg0, C0[k]);
-            out[3 * pix + 1] = fmaf(T[k], bg1, C1[k]);
-            out[3 * pix + 2] = fmaf(T[k], bg2, C2[k]);
-            if (final_T) final_T[pix] = T[k];
-            if (last) last[pix] = lastc[k];
-            if (n_eval) n_eval[pix] = ne[k];
+            g.out[3 * pix + 0] = fmaf(T[k], g.bg0, C0[k]);
+            g.out[3 * pix + 1] = fmaf(T[k], g.bg1, C1[k]);
+            g.out[3 * pix + 2] = fmaf(T[k], g.bg2, C2[k]);
+            if (g.final_T) g.final_T[pix] = T[k];
+            if (g.last) g.last[pix] = lastc[k];
+            if (g.n_eval) g.n_eval[pix] = ne[k];
         }
     }
 }
 
-template <int KIND>
-void launch_render(int ppt, int blocks, int threads, cudaStream_t s, const CamTable &t, const CfgDev &c,
-                   const float4 *rec, const uint32_t *vals, const uint2 *rg, uint32_t nrec,
-                   const float *bg, float *out, float *fT, uint32_t *last, uint32_t *ne)
+template <int KIND, int PPT>
+__global__ void __launch_bounds__(256 / PPT)
+render_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
+              const __grid_constant__ RenderArgs g)
 {
-    if (ppt == 4)
-        render_kernel<KIND, 4><<<blocks, threads, 0, s>>>(t, c, rec, vals, rg, nrec, bg[0], bg[1], bg[2], out, fT, last, ne);
-    else if (ppt == 2)
-        render_kernel<KIND, 2><<<blocks, threads, 0, s>>>(t, c, rec, vals, rg, nrec, bg[0], bg[1], bg[2], out, fT, last, ne);
-    else
-        render_kernel<KIND, 1><<<blocks, threads, 0, s>>>(t, c, rec, vals, rg, nrec, bg[0], bg[1], bg[2], out, fT, last, ne);
+    __shared__ float4 s_a[kMaxBatch];
+    __shared__ float4 s_b[kMaxBatch];
+    __shared__ float4 s_c[kMaxBatch];
+    render_tile<KIND, PPT>(cams, cfg, g, blockIdx.x, s_a, s_b, s_c);
+}
+
+template <int KIND, int PPT>
+__global__ void __launch_bounds__(256 / PPT)
+render_persistent_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
+                         const __grid_constant__ RenderArgs g, uint32_t *work)
+{
+    __shared__ float4 s_a[kMaxBatch];
+    __shared__ float4 s_b[kMaxBatch];
+    __shared__ float4 s_c[kMaxBatch];
+    __shared__ uint32_t s_tile;
+    while (true) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(work, 1u);
+        __syncthreads();
+        const uint32_t t = s_tile;
+        __syncthreads(); // every thread has read s_tile before it is overwritten
+        if (t >= (uint32_t)cams.total_tiles) break;
+        render_tile<KIND, PPT>(cams, cfg, g, (int)t, s_a, s_b, s_c);
+    }
+}
+
+template <int KIND, int PPT>
+cudaError_t launch2(int threads, cudaStream_t s, const CamTable &t, const CfgDev &c, const RenderArgs &g,
+                    uint32_t *work)
+{
+    if (!work) {
+        render_kernel<KIND, PPT><<<t.total_tiles, threads, 0, s>>>(t, c, g);
+        return cudaPeekAtLastError();
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_persistent_kernel<KIND, PPT>,
+                                                      threads, 0) != cudaSuccess)
+        return cudaGetLastError();
+    const int grid = std::max(1, std::min(t.total_tiles, sms * std::max(per_sm, 1)));
+    cudaError_t e = cudaMemsetAsync(work, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    render_persistent_kernel<KIND, PPT><<<grid, threads, 0, s>>>(t, c, g, work);
+    return cudaPeekAtLastError();
+}
+
+template <int KIND>
+cudaError_t launch_render(int ppt, int threads, cudaStream_t s, const CamTable &t, const CfgDev &c,
+                          const RenderArgs &g, uint32_t *work)
+{
+    if (ppt == 4) return launch2<KIND, 4>(threads, s, t, c, g, work);
+    if (ppt == 2) return launch2<KIND, 2>(threads, s, t, c, g, work);
+    return launch2<KIND, 1>(threads, s, t, c, g, work);
 }
 
 } // namespace
@@ -144,33 +204,50 @@ void launch_render(int ppt, int blocks, int threads, cudaStream_t s, const CamTa
 
 using namespace gs;
 
+extern "C" size_t gs_render_work_bytes(void) { return 256; }
+
 extern "C" gs_status gs_render(void *stream, const gs_camera *cams, int32_t ncam, int32_t P,
                                const gs_config *cfg, const void *d_splat2d, const uint32_t *d_vals,
                                const uint32_t *d_ranges, const float *bg, float *d_out_rgb,
-                               float *d_final_T, uint32_t *d_last, uint32_t *d_n_eval)
+                               float *d_final_T, uint32_t *d_last, uint32_t *d_n_eval,
+                               void *d_work)
 {
     if (!cams || !cfg || !bg || ncam <= 0 || ncam > kMaxCams || P < 0) return GS_ERR_ARG;
     if (!d_ranges || !d_out_rgb || (P > 0 && (!d_splat2d || !d_vals))) return GS_ERR_ARG;
+    if (d_work && ((uintptr_t)d_work & 3)) return GS_ERR_ARG;
     CamTable t;
     CfgDev c;
     if (!build_cam_table(cams, ncam, cfg, &t) || !build_cfg(cfg, &c)) return GS_ERR_ARG;
     const int ppt = cfg->px_per_thread;
     if (ppt != 1 && ppt != 2 && ppt != 4) return GS_ERR_ARG;
+    if (cfg->batch < 1 || cfg->batch > kMaxBatch) return GS_ERR_ARG;
     if (cfg->fp16x2) return GS_ERR_UNSUPPORTED;
     if (cfg->tile_w % ppt) return GS_ERR_ARG;
     const int threads = cfg->tile_w * cfg->tile_h / ppt;
     if (t.total_tiles == 0) return GS_OK;
-    const float4 *rec = P > 0 ? splat2d_const(d_splat2d, (int64_t)ncam * P).rec : nullptr;
+    RenderArgs g;
+    g.rec = P > 0 ? splat2d_const(d_splat2d, (int64_t)ncam * P).rec : nullptr;
+    g.vals = d_vals;
+    g.ranges = reinterpret_cast<const uint2 *>(d_ranges);
+    g.n_records = (uint32_t)((int64_t)ncam * P);
+    g.bg0 = bg[0]; g.bg1 = bg[1]; g.bg2 = bg[2];
+    g.out = d_out_rgb;
+    g.final_T = d_final_T;
+    g.last = d_last;
+    g.n_eval = d_n_eval;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const uint2 *rg = reinterpret_cast<const uint2 *>(d_ranges);
-    const uint32_t nrec = (uint32_t)((int64_t)ncam * P);
+    uint32_t *work = static_cast<uint32_t *>(d_work);
+    cudaError_t e;
     switch (cfg->kind) {
-    case GS_K_EXP: launch_render<GS_K_EXP>(ppt, t.total_tiles, threads, s, t, c, rec, d_vals, rg, nrec, bg, d_out_rgb, d_final_T, d_last, d_n_eval); break;
-    case GS_K_POLY1: launch_render<GS_K_POLY1>(ppt, t.total_tiles, threads, s, t, c, rec, d_vals, rg, nrec, bg, d_out_rgb, d_final_T, d_last, d_n_eval); break;
-    case GS_K_POLY2: launch_render<GS_K_POLY2>(ppt, t.total_tiles, threads, s, t, c, rec, d_vals, rg, nrec, bg, d_out_rgb, d_final_T, d_last, d_n_eval); break;
-    default: launch_render<GS_K_POLY3>(ppt, t.total_tiles, threads, s, t, c, rec, d_vals, rg, nrec, bg, d_out_rgb, d_final_T, d_last, d_n_eval); break;
+    case GS_K_EXP: e = launch_render<GS_K_EXP>(ppt, threads, s, t, c, g, work); break;
+    case GS_K_POLY1: e = launch_render<GS_K_POLY1>(ppt, threads, s, t, c, g, work); break;
+    case GS_K_POLY2: e = launch_render<GS_K_POLY2>(ppt, threads, s, t, c, g, work); break;
+    default: e = launch_render<GS_K_POLY3>(ppt, threads, s, t, c, g, work); break;
     }
     count_launch();
-    GS_LAUNCH_CHECK();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return GS_ERR_CUDA;
+    }
     return GS_OK;
 }

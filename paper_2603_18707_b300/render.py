@@ -13,6 +13,8 @@ import torch
 from . import api
 from ._lib import GS_ERR_CAPACITY
 
+MAX_CAPACITY = (1 << 30) - 1  # the binning's counters hold 30 bits
+
 
 def activate(scene: dict, device="cuda") -> dict:
     """3DGS activations of raw parameters: scale = exp(log-scale), opacity =
@@ -28,7 +30,7 @@ class Rasterizer:
     """Renders P splats into a fixed list of cameras (at most 64)."""
 
     def __init__(self, cams, cfg, P: int, capacity: int | None = None, device="cuda",
-                 keep_keys: bool = False):
+                 keep_keys: bool = False, persistent: bool = False):
         self.cams = api.camera_array(cams)
         self.ncam = len(self.cams)
         self.cfg = cfg
@@ -47,9 +49,10 @@ class Rasterizer:
         self.last = torch.empty(self.npix, **i32)
         self.n_eval = torch.empty(self.npix, **i32)
         self.keep_keys = keep_keys
+        self.work = (torch.zeros(api.gs_render_work_bytes(), **u8) if persistent else None)
         self.shrink = capacity is None  # an explicit capacity is kept as given
         self.capacity = 0
-        self._alloc(capacity if capacity else max(1 << 20, 8 * self.ncam * self.P))
+        self._alloc(capacity if capacity else min(max(1 << 20, 8 * self.ncam * self.P), MAX_CAPACITY))
 
     def _alloc(self, capacity: int):
         self.capacity = int(capacity)
@@ -70,7 +73,8 @@ class Rasterizer:
 
     def blend(self, bg=(0.0, 0.0, 0.0), n_eval: bool = True):
         api.gs_render(self.cams, self.P, self.cfg, self.splat2d, self.vals, self.ranges, bg,
-                      self.out, self.final_T, self.last, self.n_eval if n_eval else None)
+                      self.out, self.final_T, self.last, self.n_eval if n_eval else None,
+                      self.work)
 
     def forward(self, sc: dict, bg=(0.0, 0.0, 0.0), n_eval: bool = True):
         """One pass of the whole path; grows the overlap buffer when it was
@@ -89,7 +93,9 @@ class Rasterizer:
                     self._alloc(int(need * 1.15) + 4096)
                     continue
                 return self.out
-            self._alloc(int(max(need, self.capacity) * 1.25) + 1024)
+            if self.capacity >= MAX_CAPACITY:
+                raise RuntimeError("more than 2^30 - 1 tile overlaps: split the camera batch")
+            self._alloc(min(int(max(need, self.capacity) * 1.25) + 1024, MAX_CAPACITY))
         raise RuntimeError("overlap capacity could not be sized")
 
     def run_async(self, sc: dict, bg=(0.0, 0.0, 0.0), n_eval: bool = False):
@@ -99,6 +105,22 @@ class Rasterizer:
         self.bin_sort()
         self.blend(bg, n_eval)
         return self.out
+
+    def capture(self, sc: dict, bg=(0.0, 0.0, 0.0), n_eval: bool = False):
+        """CUDA graph of one whole pass (every launch and memset of
+        preprocess, bin/sort and blend) over the given, fixed input tensors.
+        Call forward() first so that the buffers are sized; replay with
+        graph.replay()."""
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.run_async(sc, bg, n_eval)  # warm-up on the capture stream
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self.run_async(sc, bg, n_eval)
+        return graph
 
     def images(self):
         out, o = [], 0

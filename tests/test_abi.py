@@ -114,7 +114,15 @@ def test_host_argument_checks(L):
     assert lb.gs_bin_sort(None, cams, 1, 10, C.byref(cfg), ptr, 1 << 31, ptr, 1 << 40, ptr, ptr, None, None) == GS_ERR_ARG
     assert lb.gs_bin_sort(None, cams, 1, 10, C.byref(cfg), ptr, 100, C.c_void_p(300), 1 << 30, ptr, ptr, None, None) == GS_ERR_ARG
     bg = (C.c_float * 3)(0, 0, 0)
-    assert lb.gs_render(None, cams, 1, 10, C.byref(cfg), None, None, None, bg, None, None, None, None) == GS_ERR_ARG
+    assert lb.gs_render(None, cams, 1, 10, C.byref(cfg), None, None, None, bg, None, None, None, None,
+                        None) == GS_ERR_ARG
+    bad = api.make_config("poly1", "opacity")
+    bad.batch = 512
+    assert lb.gs_render(None, cams, 1, 10, C.byref(bad), ptr, ptr, ptr, bg, ptr, None, None, None,
+                        None) == GS_ERR_ARG
+    bad = api.make_config("poly1", "opacity", px_per_thread=3)
+    assert lb.gs_render(None, cams, 1, 10, C.byref(bad), ptr, ptr, ptr, bg, ptr, None, None, None,
+                        None) == GS_ERR_ARG
     code = C.c_int32()
     assert lb.gs_workspace_status(None, None, C.byref(code)) == GS_ERR_ARG
     assert lb.gs_status_string(4) == b"overlap capacity exceeded"

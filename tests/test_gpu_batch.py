@@ -1,0 +1,119 @@
+"""Batched multi-camera rendering: persistent launch, CUDA-graph replay,
+mixed resolutions, staging depth, and the autotuner."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gs():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2603_18707_b300 import build
+    build.build()
+    from paper_2603_18707_b300 import api, render, synth
+    return api, render, synth
+
+
+def _mixed_small(synth):
+    # the 4:3:2:1 resolution mix of the serving workload, scaled down 4x
+    return [synth.look_at(_pos(c), [0, 0, 0], c["width"] // 4, c["height"] // 4)
+            for c in synth.mixed_cameras(10)]
+
+
+def _pos(c):
+    vm = np.asarray(c["viewmat"])
+    return -vm[:3, :3].T @ vm[:3, 3]
+
+
+@pytest.fixture(scope="module")
+def scene(gs):
+    api, render, synth = gs
+    raw = synth.scene_clusters(200_000, 2, sh_degree=3)
+    return raw, render.activate(raw)
+
+
+def test_persistent_launch_matches_per_tile_launch(gs, scene):
+    api, render, synth = gs
+    raw, sc = scene
+    cams = _mixed_small(synth)
+    for kind in ("poly1", "exp"):
+        cfg = api.make_config(kind, "opacity")
+        a = render.Rasterizer(cams, cfg, 200_000)
+        b = render.Rasterizer(cams, cfg, 200_000, persistent=True)
+        a.forward(sc)
+        b.forward(sc)
+        torch.cuda.synchronize()
+        assert torch.equal(a.out, b.out) and torch.equal(a.last, b.last)
+        assert torch.equal(a.n_eval, b.n_eval)
+
+
+def test_mixed_batch_equals_single_cameras(gs, scene):
+    api, render, synth = gs
+    raw, sc = scene
+    cams = _mixed_small(synth)
+    cfg = api.make_config("poly1", "opacity")
+    R = render.Rasterizer(cams, cfg, 200_000, persistent=True)
+    R.forward(sc)
+    imgs = [im.clone() for im in R.images()]
+    for cam, im in zip(cams, imgs):
+        one = render.Rasterizer([cam], cfg, 200_000)
+        one.forward(sc)
+        assert torch.equal(one.images()[0], im)
+
+
+def test_graph_replay_matches_eager(gs, scene):
+    api, render, synth = gs
+    raw, sc = scene
+    cams = _mixed_small(synth)
+    cfg = api.make_config("poly1", "opacity")
+    R = render.Rasterizer(cams, cfg, 200_000, persistent=True)
+    static = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in sc.items()}
+    R.forward(static)
+    eager = R.out.clone()
+    graph = R.capture(static)
+    R.out.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(R.out, eager)
+    # new inputs written in place are picked up by the replay
+    static["means"].add_(0.01)
+    graph.replay()
+    torch.cuda.synchronize()
+    replayed = R.out.clone()
+    ref = render.Rasterizer(cams, cfg, 200_000, capacity=R.capacity)
+    ref.forward(static)
+    assert torch.equal(replayed, ref.out)
+    assert not torch.equal(replayed, eager)
+
+
+def test_batch_depth_does_not_change_pixels(gs, scene):
+    api, render, synth = gs
+    raw, sc = scene
+    cams = _mixed_small(synth)[:3]
+    outs = []
+    for b in (256, 100, 32):
+        R = render.Rasterizer(cams, api.make_config("poly3", "opacity", batch=b), 200_000)
+        R.forward(sc)
+        outs.append(R.out.clone())
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
+def test_autotuner_picks_a_measured_candidate_and_caches(gs, scene, tmp_path):
+    api, render, synth = gs
+    from paper_2603_18707_b300 import autotune
+    raw, sc = scene
+    cams = _mixed_small(synth)[:4]
+    cache = str(tmp_path / "tune.json")
+    r1 = autotune.autotune(cams, "poly1", "opacity", sc, 200_000, steps=2, cache=cache)
+    assert tuple(r1["tile"]) in autotune.TILES and r1["px_per_thread"] in autotune.PPTS
+    assert r1["batch"] in autotune.BATCHES
+    assert r1["ms"] == min(r1["trials_ms"].values())
+    assert len(r1["trials_ms"]) == len(autotune.TILES) * len(autotune.PPTS) + len(autotune.BATCHES) - 1
+    r2 = autotune.autotune(cams, "poly1", "opacity", sc, 200_000, steps=2, cache=cache)
+    assert r2 == r1
+    R = render.Rasterizer(cams, api.make_config("poly1", "opacity", **autotune.config_overrides(r1)),
+                          200_000)
+    R.forward(sc)
+    assert torch.isfinite(R.out).all()
