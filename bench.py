@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-diff", action="store_true", help="skip the differentiable-render leg")
     p.add_argument("--no-batched", action="store_true", help="skip the 64-camera batched leg")
+    p.add_argument("--no-fp16", action="store_true", help="skip the FP16x2 precision leg")
     p.add_argument("--ppt", type=int, default=None, help="pixels per blend thread (1, 2, 4)")
     p.add_argument("--tile", type=str, default=None, help="tile shape WxH, e.g. 16x16")
     p.add_argument("--profile", choices=["poly1", "exp", "poly2", "poly3"], default=None,
@@ -338,13 +339,17 @@ def run_ours(a, world, rank, local):
                 "dominant_stage": dom}
 
     extra = {}
-    if not a.no_diff:
-        del R, sc
+    del R, sc
+    for name, on, fn in (("differentiable", not a.no_diff, bench_differentiable),
+                         ("batched", not a.no_batched, bench_batched),
+                         ("fp16x2", not a.no_fp16, bench_fp16x2)):
+        if not on:
+            continue
         torch.cuda.empty_cache()
-        extra["differentiable"] = bench_differentiable(a)
-    if not a.no_batched:
-        torch.cuda.empty_cache()
-        extra["batched"] = bench_batched(a)
+        try:
+            extra[name] = fn(a)
+        except Exception as exc:  # noqa: BLE001 - a failed extra leg must not lose the headline
+            extra[name] = {"error": f"{type(exc).__name__}: {exc}"}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
@@ -419,6 +424,44 @@ def bench_differentiable(a):
     return {"workload": "1M-splat cluster scene, SH degree 3, 1024x1024, f1 + opacity cull, L1 loss",
             "ms_forward_backward": ms, "ms_forward": ms_fwd, "steps_per_s": 1e3 / ms,
             "note": "forward includes the overlap-count read-back of Rasterizer.forward"}
+
+
+def bench_fp16x2(a):
+    """Precision variant on the headline workload (3M splats, 16 cameras,
+    1920x1080): f1 and f'2 with the quadric and polynomial in packed FP16x2,
+    colour and transmittance in FP32. Timed like the headline; errors against
+    the FP32 GPU render of the same frames (the FP64-oracle comparison lives
+    in the test suite)."""
+    import numpy as np
+    import torch
+
+    from paper_2603_18707_b300 import api, render, synth
+    raw = synth.scene_clusters(a.splats, 0, sh_degree=3)
+    cams = synth.orbit_cameras(a.cams, a.width, a.height)
+    sc = render.activate(raw)
+    out = {}
+    for kind in ("poly1", "poly2"):
+        res = {}
+        imgs = {}
+        for half in (0, 1):
+            R = render.Rasterizer(cams, api.make_config(kind, "opacity", fp16x2=half, px_per_thread=2),
+                                  a.splats)
+            R.forward(sc, n_eval=False)
+            imgs[half] = R.out.clone()
+            for _ in range(3):
+                R.run_async(sc)
+            res[half] = _events_ms(lambda: R.run_async(sc), max(5, a.steps // 6))
+            del R
+        err = (imgs[1].double() - imgs[0].double()).abs()
+        mse = float((err ** 2).mean())
+        out[kind] = {"frames_per_s_fp16x2": a.cams / (res[1] / 1e3),
+                     "frames_per_s_fp32": a.cams / (res[0] / 1e3),
+                     "vs_fp32": {"max": float(err.max()), "mean": float(err.mean()),
+                                 "mean_per_channel": [float(v) for v in err.mean(0)],
+                                 "max_per_channel": [float(v) for v in err.max(0).values],
+                                 "psnr_db": float(-10 * np.log10(max(mse, 1e-30))),
+                                 "frac_px_above_2e-3": float((err.max(-1).values > 2e-3).double().mean())}}
+    return out
 
 
 def bench_batched(a):

@@ -22,6 +22,8 @@
 // launch for any mix of resolutions, balanced dynamically).
 #include <algorithm>
 
+#include <cuda_fp16.h>
+
 #include "blend_math.cuh"
 
 namespace gs {
@@ -41,9 +43,35 @@ struct RenderArgs {
     uint32_t *n_eval;
 };
 
-template <int KIND, int PPT>
+// FP16x2 alpha of a pixel pair (u_a, u_b computed in FP32, sharing v^2):
+// Q = u^2 + v^2 and the opacity-folded kernel in packed half2 FMAs.
+// Q is clamped to the cut x0 before f'2's polynomial so that an overflowing
+// Q (a far-away splat) gives 0 rather than inf * 0.
+template <int KIND>
+__device__ __forceinline__ float2 alpha_pair_h2(float ua, float ub, __half2 v2h, uint4 hp, __half2 x0h,
+                                                __half2 amaxh)
+{
+    const __half2 p0 = *reinterpret_cast<__half2 *>(&hp.x), p1 = *reinterpret_cast<__half2 *>(&hp.y);
+    const __half2 p2 = *reinterpret_cast<__half2 *>(&hp.z), p3 = *reinterpret_cast<__half2 *>(&hp.w);
+    const __half2 u2 = __floats2half2_rn(ua, ub);
+    const __half2 Q = __hfma2(u2, u2, v2h);
+    __half2 al;
+    if (KIND == GS_K_EXP) {
+        al = h2exp2(__hfma2(p1, Q, p0));
+    } else if (KIND == GS_K_POLY1) {
+        al = __hfma2(p1, Q, p0);
+    } else if (KIND == GS_K_POLY2) {
+        const __half2 Qc = __hmin2(Q, x0h);
+        al = __hmul2(__hlt2(Q, x0h), __hfma2(__hfma2(p2, Qc, p1), Qc, p0));
+    } else {
+        al = __hfma2(__hfma2(__hfma2(p3, Q, p2), Q, p1), Q, p0);
+    }
+    return __half22float2(__hmin2(al, amaxh));
+}
+
+template <int KIND, int PPT, bool HALF>
 __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &cfg, const RenderArgs &g,
-                                            int gtile, float4 *s_a, float4 *s_b, float4 *s_c)
+                                            int gtile, float4 *s_a, float4 *s_b, float4 *s_c, uint4 *s_h)
 {
     int c = 0;
     while (c + 1 < cams.ncam && cams.cam[c + 1].tile_base <= gtile) ++c;
@@ -73,6 +101,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
         if (px0 + k < cm.W && py < cm.H) active |= 1u << k;
     }
     const float eps = cfg.eps, amax = cfg.alpha_max, tmin = cfg.t_min;
+    const __half2 x0h = __float2half2_rn(fminf(cfg.x0, 60000.f)), amaxh = __float2half2_rn(amax);
     for (uint32_t base = 0; base < n; base += B) {
         if (__syncthreads_count(active != 0) == 0) break;
         for (int i = threadIdx.x; i < B; i += nthreads) {
@@ -84,6 +113,11 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                 s_a[i] = k.a;
                 s_b[i] = k.b;
                 s_c[i] = k.c;
+                if (HALF) {
+                    const __half2 h[4] = {__float2half2_rn(k.b.y), __float2half2_rn(k.b.z),
+                                          __float2half2_rn(k.b.w), __float2half2_rn(k.c.w)};
+                    s_h[i] = *reinterpret_cast<const uint4 *>(h);
+                }
             }
         }
         __syncthreads();
@@ -97,12 +131,26 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
             const float p3 = (KIND == GS_K_POLY3) ? s_c[j].w : 0.f; // the cubic's top coefficient
             float al[PPT];
             bool any = false;
+            if (HALF) {
+                const uint4 hp = s_h[j];
+                const __half2 v2h = __float2half2_rn(v2);
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) {
-                const float u = fmaf(a.x, xs[k], ub);
-                const float Q = fmaf(u, u, v2);
-                al[k] = fminf(amax, alpha_of_q<KIND>(cfg, b, p3, Q));
-                any |= (active >> k & 1u) && al[k] >= eps;
+                for (int k = 0; k < PPT; k += 2) {
+                    const float2 ap = alpha_pair_h2<KIND>(fmaf(a.x, xs[k], ub), fmaf(a.x, xs[k + 1], ub),
+                                                          v2h, hp, x0h, amaxh);
+                    al[k] = ap.x;
+                    al[k + 1] = ap.y;
+                }
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) any |= (active >> k & 1u) && al[k] >= eps;
+            } else {
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    const float u = fmaf(a.x, xs[k], ub);
+                    const float Q = fmaf(u, u, v2);
+                    al[k] = fminf(amax, alpha_of_q<KIND>(cfg, b, p3, Q));
+                    any |= (active >> k & 1u) && al[k] >= eps;
+                }
             }
             if (!any) continue;
             const float4 col = s_c[j];
@@ -139,7 +187,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
     }
 }
 
-template <int KIND, int PPT>
+template <int KIND, int PPT, bool HALF>
 __global__ void __launch_bounds__(256 / PPT)
 render_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
               const __grid_constant__ RenderArgs g)
@@ -147,10 +195,11 @@ render_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ Cfg
     __shared__ float4 s_a[kMaxBatch];
     __shared__ float4 s_b[kMaxBatch];
     __shared__ float4 s_c[kMaxBatch];
-    render_tile<KIND, PPT>(cams, cfg, g, blockIdx.x, s_a, s_b, s_c);
+    __shared__ uint4 s_h[HALF ? kMaxBatch : 1];
+    render_tile<KIND, PPT, HALF>(cams, cfg, g, blockIdx.x, s_a, s_b, s_c, s_h);
 }
 
-template <int KIND, int PPT>
+template <int KIND, int PPT, bool HALF>
 __global__ void __launch_bounds__(256 / PPT)
 render_persistent_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
                          const __grid_constant__ RenderArgs g, uint32_t *work)
@@ -158,6 +207,7 @@ render_persistent_kernel(const __grid_constant__ CamTable cams, const __grid_con
     __shared__ float4 s_a[kMaxBatch];
     __shared__ float4 s_b[kMaxBatch];
     __shared__ float4 s_c[kMaxBatch];
+    __shared__ uint4 s_h[HALF ? kMaxBatch : 1];
     __shared__ uint32_t s_tile;
     while (true) {
         if (threadIdx.x == 0) s_tile = atomicAdd(work, 1u);
@@ -165,38 +215,42 @@ render_persistent_kernel(const __grid_constant__ CamTable cams, const __grid_con
         const uint32_t t = s_tile;
         __syncthreads(); // every thread has read s_tile before it is overwritten
         if (t >= (uint32_t)cams.total_tiles) break;
-        render_tile<KIND, PPT>(cams, cfg, g, (int)t, s_a, s_b, s_c);
+        render_tile<KIND, PPT, HALF>(cams, cfg, g, (int)t, s_a, s_b, s_c, s_h);
     }
 }
 
-template <int KIND, int PPT>
+template <int KIND, int PPT, bool HALF>
 cudaError_t launch2(int threads, cudaStream_t s, const CamTable &t, const CfgDev &c, const RenderArgs &g,
                     uint32_t *work)
 {
     if (!work) {
-        render_kernel<KIND, PPT><<<t.total_tiles, threads, 0, s>>>(t, c, g);
+        render_kernel<KIND, PPT, HALF><<<t.total_tiles, threads, 0, s>>>(t, c, g);
         return cudaPeekAtLastError();
     }
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_persistent_kernel<KIND, PPT>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_persistent_kernel<KIND, PPT, HALF>,
                                                       threads, 0) != cudaSuccess)
         return cudaGetLastError();
     const int grid = std::max(1, std::min(t.total_tiles, sms * std::max(per_sm, 1)));
     cudaError_t e = cudaMemsetAsync(work, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    render_persistent_kernel<KIND, PPT><<<grid, threads, 0, s>>>(t, c, g, work);
+    render_persistent_kernel<KIND, PPT, HALF><<<grid, threads, 0, s>>>(t, c, g, work);
     return cudaPeekAtLastError();
 }
 
 template <int KIND>
-cudaError_t launch_render(int ppt, int threads, cudaStream_t s, const CamTable &t, const CfgDev &c,
-                          const RenderArgs &g, uint32_t *work)
+cudaError_t launch_render(int ppt, bool half, int threads, cudaStream_t s, const CamTable &t,
+                          const CfgDev &c, const RenderArgs &g, uint32_t *work)
 {
-    if (ppt == 4) return launch2<KIND, 4>(threads, s, t, c, g, work);
-    if (ppt == 2) return launch2<KIND, 2>(threads, s, t, c, g, work);
-    return launch2<KIND, 1>(threads, s, t, c, g, work);
+    if (half) {
+        if (ppt == 4) return launch2<KIND, 4, true>(threads, s, t, c, g, work);
+        return launch2<KIND, 2, true>(threads, s, t, c, g, work);
+    }
+    if (ppt == 4) return launch2<KIND, 4, false>(threads, s, t, c, g, work);
+    if (ppt == 2) return launch2<KIND, 2, false>(threads, s, t, c, g, work);
+    return launch2<KIND, 1, false>(threads, s, t, c, g, work);
 }
 
 } // namespace
@@ -221,7 +275,8 @@ extern "C" gs_status gs_render(void *stream, const gs_camera *cams, int32_t ncam
     const int ppt = cfg->px_per_thread;
     if (ppt != 1 && ppt != 2 && ppt != 4) return GS_ERR_ARG;
     if (cfg->batch < 1 || cfg->batch > kMaxBatch) return GS_ERR_ARG;
-    if (cfg->fp16x2) return GS_ERR_UNSUPPORTED;
+    const bool half = cfg->fp16x2 != 0;
+    if (half && ppt == 1) return GS_ERR_ARG; // packed pairs need 2 or 4 pixels per thread
     if (cfg->tile_w % ppt) return GS_ERR_ARG;
     const int threads = cfg->tile_w * cfg->tile_h / ppt;
     if (t.total_tiles == 0) return GS_OK;
@@ -239,10 +294,10 @@ extern "C" gs_status gs_render(void *stream, const gs_camera *cams, int32_t ncam
     uint32_t *work = static_cast<uint32_t *>(d_work);
     cudaError_t e;
     switch (cfg->kind) {
-    case GS_K_EXP: e = launch_render<GS_K_EXP>(ppt, threads, s, t, c, g, work); break;
-    case GS_K_POLY1: e = launch_render<GS_K_POLY1>(ppt, threads, s, t, c, g, work); break;
-    case GS_K_POLY2: e = launch_render<GS_K_POLY2>(ppt, threads, s, t, c, g, work); break;
-    default: e = launch_render<GS_K_POLY3>(ppt, threads, s, t, c, g, work); break;
+    case GS_K_EXP: e = launch_render<GS_K_EXP>(ppt, half, threads, s, t, c, g, work); break;
+    case GS_K_POLY1: e = launch_render<GS_K_POLY1>(ppt, half, threads, s, t, c, g, work); break;
+    case GS_K_POLY2: e = launch_render<GS_K_POLY2>(ppt, half, threads, s, t, c, g, work); break;
+    default: e = launch_render<GS_K_POLY3>(ppt, half, threads, s, t, c, g, work); break;
     }
     count_launch();
     if (e != cudaSuccess) {

@@ -13,7 +13,7 @@ import torch
 from . import api
 from ._lib import GS_ERR_CAPACITY
 
-MAX_CAPACITY = (1 << 30) - 1  # the binning's counters hold 30 bits
+MAX_CAPACITY = (1 << 30) - 2  # the binning's counters hold 30 bits (< 2^30 - 1 overlaps)
 
 
 def activate(scene: dict, device="cuda") -> dict:

@@ -1,0 +1,127 @@
+"""Precision variant: quadric and polynomial in packed FP16x2 FMAs, colour and
+transmittance in FP32. Errors against the FP64 oracle and the FP32 GPU path
+are measured and reported (max / mean per channel, PSNR, and the share of
+pixels above the 2e-3 bound)."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import KIND_COEFFS, NEAR_MARGIN
+
+pytestmark = pytest.mark.gpu
+REPORT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+TOL_FP16 = 2e-3
+
+
+@pytest.fixture(scope="module")
+def gs():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2603_18707_b300 import build
+    build.build()
+    from paper_2603_18707_b300 import api, render, synth
+    return api, render, synth
+
+
+def _stats(img, ref, margin=None):
+    err = np.abs(img.astype(np.float64) - ref)
+    mse = float(np.mean(err ** 2))
+    out = {"max": float(err.max()), "mean": float(err.mean()),
+           "mean_per_channel": [float(v) for v in err.reshape(-1, 3).mean(0)],
+           "max_per_channel": [float(v) for v in err.reshape(-1, 3).max(0)],
+           "psnr_db": float(-10 * np.log10(max(mse, 1e-30))),
+           "frac_px_above_2e-3": float((err.max(-1) > TOL_FP16).mean())}
+    if margin is not None:
+        far = margin >= NEAR_MARGIN
+        out["max_outside_threshold_flips"] = float(err.max(-1)[far].max(initial=0.0))
+    return out
+
+
+def _report(name, d):
+    os.makedirs(REPORT, exist_ok=True)
+    with open(os.path.join(REPORT, "fp16x2_errors.jsonl"), "a") as f:
+        f.write(json.dumps({"case": name, **d}) + "\n")
+
+
+@pytest.mark.parametrize("kind", ["poly1", "poly2", "poly3", "exp"])
+def test_fp16x2_small_scene_against_oracle(gs, orc, kind):
+    api, render, synth = gs
+    raw = synth.scene_uniform(4096, 0)
+    cam = synth.camera_small()
+    sc = render.activate(raw)
+    imgs = {}
+    for half in (0, 1):
+        R = render.Rasterizer([cam], api.make_config(kind, "opacity", fp16x2=half, px_per_thread=2), 4096)
+        R.forward(sc)
+        imgs[half] = R.images()[0].cpu().numpy()
+    oc = orc.camera_from_dict(cam)
+    osc = orc.activate(raw)
+    ref, _, _ = orc.render_untiled(osc, oc, orc.make_config(kind, KIND_COEFFS[kind], "opacity"))
+    *_, margin = orc.render_tiled(osc, oc, orc.make_config(kind, KIND_COEFFS[kind], "universal"),
+                                  with_margin=True)
+    s_orc = _stats(imgs[1], ref, margin)
+    s_fp32 = _stats(imgs[1], imgs[0].astype(np.float64))
+    _report(f"small-{kind}", {"vs_oracle": s_orc, "vs_fp32": s_fp32})
+    assert s_orc["mean"] < 2e-4
+    assert s_orc["frac_px_above_2e-3"] < 0.01
+    assert s_orc["psnr_db"] > 55
+
+
+@pytest.mark.parametrize("kind", ["poly1", "poly2"])
+def test_fp16x2_full_scene_sampled_tiles(gs, orc, kind):
+    """3M-splat 1920x1080 scene, camera 0: FP16x2 vs FP32 GPU over the whole
+    frame, and vs the FP64 oracle on 24 sampled tiles."""
+    api, render, synth = gs
+    raw = synth.scene_clusters(3_000_000, 0, sh_degree=3)
+    cam = synth.orbit_cameras(16, 1920, 1080)[0]
+    sc = render.activate(raw)
+    imgs = {}
+    for half in (0, 1):
+        R = render.Rasterizer([cam], api.make_config(kind, "opacity", fp16x2=half, px_per_thread=2),
+                              3_000_000)
+        R.forward(sc)
+        imgs[half] = R.images()[0].cpu().numpy()
+        del R
+    oc = orc.camera_from_dict(cam)
+    tx, ty = 120, 68
+    rng = np.random.default_rng(0)
+    tiles = sorted(set(rng.integers(0, tx * ty, 20).tolist()) | {0, tx - 1, (ty - 1) * tx, tx * ty - 1})
+    ref, _, _, _, _, margin = orc.render_tiled(orc.activate(raw), oc,
+                                               orc.make_config(kind, KIND_COEFFS[kind], "opacity"),
+                                               tiles=tiles, with_margin=True)
+    mask = np.zeros((1080, 1920), bool)
+    for t in tiles:
+        y, x = (t // tx) * 16, (t % tx) * 16
+        mask[y:y + 16, x:x + 16] = True
+    s_orc = _stats(imgs[1][mask], ref[mask], margin[mask])
+    s_fp32 = _stats(imgs[1], imgs[0].astype(np.float64))
+    _report(f"3M-1080p-{kind}", {"vs_oracle_sampled_tiles": s_orc, "vs_fp32_full_frame": s_fp32})
+    assert s_orc["mean"] < 2e-4 and s_fp32["mean"] < 2e-4
+    assert s_orc["frac_px_above_2e-3"] < 0.01 and s_fp32["frac_px_above_2e-3"] < 0.01
+
+
+def test_fp16x2_persistent_and_backward_refusal(gs):
+    api, render, synth = gs
+    from paper_2603_18707_b300._lib import GS_ERR_UNSUPPORTED, GsError
+    raw = synth.scene_uniform(4096, 1)
+    cams = [synth.camera_small(128, 128), synth.camera_small(100, 75)]
+    sc = render.activate(raw)
+    cfg = api.make_config("poly1", "opacity", fp16x2=1, px_per_thread=4)
+    a = render.Rasterizer(cams, cfg, 4096)
+    b = render.Rasterizer(cams, cfg, 4096, persistent=True)
+    a.forward(sc)
+    b.forward(sc)
+    assert torch.equal(a.out, b.out)
+    c2 = render.Rasterizer(cams, api.make_config("poly1", "opacity", fp16x2=1, px_per_thread=2), 4096)
+    c2.forward(sc)
+    assert torch.equal(a.out, c2.out)  # pairs are packed the same way for 2 and 4 pixels per thread
+    g = {k: torch.zeros_like(sc[k]) for k in ("means", "scales", "quats", "opacities", "sh")}
+    grad2d = torch.empty(api.gs_grad2d_bytes(2, 4096), dtype=torch.uint8, device="cuda")
+    with pytest.raises(GsError) as e:
+        api.gs_render_backward(a.cams, 4096, cfg, sc["means"], sc["scales"], sc["quats"],
+                               sc["opacities"], sc["sh"], 0, a.splat2d, a.vals, a.ranges,
+                               (0, 0, 0), a.final_T, a.last, torch.zeros_like(a.out), grad2d,
+                               g["means"], g["scales"], g["quats"], g["opacities"], g["sh"])
+    assert e.value.status == GS_ERR_UNSUPPORTED
