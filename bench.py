@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--no-fp16", action="store_true", help="skip the FP16x2 precision leg")
     p.add_argument("--ppt", type=int, default=None, help="pixels per blend thread (1, 2, 4)")
     p.add_argument("--tile", type=str, default=None, help="tile shape WxH, e.g. 16x16")
+    p.add_argument("--rect", choices=["aabb", "circle", "ellipse"], default=None,
+                   help="tile binning around the support ellipse")
     p.add_argument("--profile", choices=["poly1", "exp", "poly2", "poly3"], default=None,
                    help="run only `steps` passes of one arm (for ncu), print no bench line")
     return p.parse_args()
@@ -226,6 +228,8 @@ def run_ours(a, world, rank, local):
         over["px_per_thread"] = a.ppt
     if a.tile:
         over["tile"] = tuple(int(v) for v in a.tile.split("x"))
+    if a.rect:
+        over["rect"] = a.rect
     if a.profile:
         # profiling mode: one arm, buffers sized, then exactly `steps` passes
         r = render.Rasterizer(cams, api.make_config(a.profile, "opacity", **over), P)

@@ -72,10 +72,14 @@ typedef enum { GS_K_EXP = 0, GS_K_POLY1 = 1, GS_K_POLY2 = 2, GS_K_POLY3 = 3 } gs
  *                     pixel-exact for exp */
 typedef enum { GS_CULL_UNIVERSAL = 0, GS_CULL_OPACITY = 1, GS_CULL_LEGACY3 = 2 } gs_cull;
 
-/* Screen rectangle around the support ellipse {d : d^T conic d <= x_cut}:
- * its exact axis-aligned bounding box, or the 3DGS square around the circle
- * of radius sqrt(x_cut * lambda_max). Both are conservative. */
-typedef enum { GS_RECT_AABB = 0, GS_RECT_CIRCLE = 1 } gs_rect_mode;
+/* Which tiles a splat is binned to, around its support ellipse
+ * {d : d^T conic d <= x_cut}: every tile of the ellipse's exact axis-aligned
+ * bounding box (AABB); of the 3DGS square around the circle of radius
+ * sqrt(x_cut * lambda_max) (CIRCLE); or, per tile row, only the tiles whose
+ * pixel centres the ellipse can reach (ELLIPSE: the per-tile test of
+ * StopThePop that the paper's Baseline uses, Sec. 2.1, done analytically row
+ * by row). All three are conservative: the image is the same. */
+typedef enum { GS_RECT_AABB = 0, GS_RECT_CIRCLE = 1, GS_RECT_ELLIPSE = 2 } gs_rect_mode;
 
 /* Pinhole camera. viewmat: world -> camera, row-major 4x4; camera looks
  * along +z with +x right and +y down. A world point p maps to

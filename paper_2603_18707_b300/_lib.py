@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libgs_b300.so")
 GS_OK, GS_ERR_ARG, GS_ERR_CUDA, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, GS_ERR_UNSUPPORTED = 0, 1, 2, 4, 8, 16
 GS_K_EXP, GS_K_POLY1, GS_K_POLY2, GS_K_POLY3 = 0, 1, 2, 3
 GS_CULL_UNIVERSAL, GS_CULL_OPACITY, GS_CULL_LEGACY3 = 0, 1, 2
-GS_RECT_AABB, GS_RECT_CIRCLE = 0, 1
+GS_RECT_AABB, GS_RECT_CIRCLE, GS_RECT_ELLIPSE = 0, 1, 2
 GS_MAX_CAMERAS = 64
 
 KIND = {"exp": GS_K_EXP, "poly1": GS_K_POLY1, "poly2": GS_K_POLY2, "poly3": GS_K_POLY3}

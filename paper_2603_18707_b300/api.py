@@ -55,7 +55,8 @@ def make_config(kind="poly1", cull="opacity", **over) -> GsConfig:
         elif key == "aa":
             cfg.aa_normalize = int(bool(val))
         elif key == "rect":
-            cfg.rect_mode = {"aabb": _lib.GS_RECT_AABB, "circle": _lib.GS_RECT_CIRCLE}[val]
+            cfg.rect_mode = {"aabb": _lib.GS_RECT_AABB, "circle": _lib.GS_RECT_CIRCLE,
+                             "ellipse": _lib.GS_RECT_ELLIPSE}[val]
         else:
             setattr(cfg, key, val)
     return cfg

@@ -37,9 +37,15 @@ def _key(cams, kind, cull, P, persistent):
 
 
 def _time(cams, kind, cull, sc, P, over, persistent, steps):
+    """ms per pass, or inf for a candidate this workload cannot run (e.g.
+    small tiles pushing the overlap count past the binning's 2^30 limit)."""
     cfg = api.make_config(kind, cull, **over)
-    R = Rasterizer(cams, cfg, P, persistent=persistent)
-    R.forward(sc, n_eval=False)
+    try:
+        R = Rasterizer(cams, cfg, P, persistent=persistent)
+        R.forward(sc, n_eval=False)
+    except RuntimeError:
+        torch.cuda.synchronize()
+        return float("inf")
     torch.cuda.synchronize()
     R.run_async(sc)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -82,7 +88,9 @@ def autotune(cams, kind: str, cull: str, sc: dict, P: int, persistent: bool = Fa
     best_over = trials[best_name][1]
     result = {"tile": list(best_over["tile"]), "batch": int(best_over["batch"]),
               "px_per_thread": int(best_over["px_per_thread"]), "ms": trials[best_name][0],
-              "trials_ms": {k: v[0] for k, v in trials.items()}}
+              "trials_ms": {k: (v[0] if v[0] != float("inf") else None) for k, v in trials.items()}}
+    if result["ms"] == float("inf"):
+        raise RuntimeError("no candidate launch shape can run this workload")
     if verbose:
         print(json.dumps(result))
     if cache:

@@ -435,11 +435,15 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
     }
 }
 
-// 3. overlap emission in depth order, plus the tile-digit histograms.
+// 3. overlap emission in depth order, plus the tile-digit histograms. ELL:
+// only the tiles of each rectangle row that the support ellipse reaches
+// (GS_RECT_ELLIPSE), else the whole rectangle.
+template <bool ELL>
 __global__ void __launch_bounds__(256)
 emit_kernel(const __grid_constant__ CamTable cams, int P, uint32_t n_records,
             const uint32_t *__restrict__ sorted_vals,
             const uint32_t *__restrict__ tiles, const ushort4 *__restrict__ rects,
+            const float4 *__restrict__ rec, int tile_w, int tile_h,
             uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, uint32_t capacity,
             WsHeader *hdr, uint32_t *state, TilePlan plan, uint32_t *__restrict__ hist)
 {
@@ -487,8 +491,70 @@ emit_kernel(const __grid_constant__ CamTable cams, int P, uint32_t n_records,
     }
     __syncthreads();
     const uint32_t part_excl = s_excl;
+    if (ELL) {
+        // two levels: the warp expands its records into tile rows (32 rows at
+        // a time), each lane finds its row's tile columns, then the warp
+        // writes those rows' tiles 32 at a time
+#pragma unroll 1
+        for (int j = 0; j < kEmitItems; ++j) {
+            const uint32_t rows = cnt[j] ? (uint32_t)(rc[j].w - rc[j].y + 1) : 0u;
+            const uint32_t r_incl = warp_incl_scan(rows);
+            const uint32_t r_total = __shfl_sync(0xffffffffu, r_incl, 31);
+            const uint32_t out_base = part_excl + warp_excl + off[j];
+            uint32_t emitted = 0;
+            for (uint32_t rb = 0; rb < r_total; rb += 32) {
+                const uint32_t r = rb + lane;
+                const uint32_t rq = min(r, r_total - 1u);
+                int e = 0;
 #pragma unroll
-    for (int j = 0; j < kEmitItems; ++j) {
+                for (int sft = 16; sft > 0; sft >>= 1) {
+                    const uint32_t c = __shfl_sync(0xffffffffu, r_incl, e + sft - 1);
+                    if (c <= rq) e += sft;
+                }
+                const uint32_t ev = __shfl_sync(0xffffffffu, v[j], e);
+                const uint32_t rexcl = __shfl_sync(0xffffffffu, r_incl - rows, e);
+                uint32_t cnt2 = 0, kb = 0;
+                if (r < r_total) {
+                    const float4 g0 = rec[3 * (size_t)ev], g1 = rec[3 * (size_t)ev + 1];
+                    const ushort4 rr = rects[ev];
+                    const CamDev &cm = cams.cam[ev / (uint32_t)P];
+                    const int ty = (int)rr.y + (int)(rq - rexcl);
+                    int c0, c1;
+                    if (row_cols(g0.x, g0.y, g1.x, g1.y, g1.z, g1.w, ty, tile_w, tile_h, cm.W, cm.H,
+                                 rr.x, rr.z, c0, c1)) {
+                        cnt2 = (uint32_t)(c1 - c0 + 1);
+                        kb = (uint32_t)cm.tile_base + (uint32_t)ty * cm.tiles_x + (uint32_t)c0;
+                    }
+                }
+                const uint32_t c_incl = warp_incl_scan(cnt2);
+                const uint32_t seg = __shfl_sync(0xffffffffu, c_incl, 31);
+                for (uint32_t b2 = 0; b2 < seg; b2 += 32) {
+                    const uint32_t p = b2 + lane;
+                    const uint32_t pq = min(p, seg - 1u);
+                    int f = 0;
+#pragma unroll
+                    for (int sft = 16; sft > 0; sft >>= 1) {
+                        const uint32_t c = __shfl_sync(0xffffffffu, c_incl, f + sft - 1);
+                        if (c <= pq) f += sft;
+                    }
+                    const uint32_t fkb = __shfl_sync(0xffffffffu, kb, f);
+                    const uint32_t fbeg = __shfl_sync(0xffffffffu, c_incl - cnt2, f);
+                    const uint32_t fv = __shfl_sync(0xffffffffu, ev, f);
+                    const uint32_t o = out_base + emitted + p;
+                    if (p < seg && o < capacity) {
+                        const uint32_t key = fkb + (pq - fbeg);
+                        keys_out[o] = key;
+                        vals_out[o] = fv;
+                        for (int q = 0; q < plan.passes; ++q)
+                            atomicAdd(&s_h[q][(key >> plan.shift[q]) & ((1u << plan.bits[q]) - 1u)], 1u);
+                    }
+                }
+                emitted += seg;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < (ELL ? 0 : kEmitItems); ++j) {
         const uint32_t w_incl = incl[j];
         const uint32_t w_total = __shfl_sync(0xffffffffu, w_incl, 31);
         const uint32_t out_base = part_excl + warp_excl + off[j];
@@ -675,9 +741,15 @@ extern "C" gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t nc
             uint32_t *ek = U(L.tk0);
             uint32_t *ev = (plan.passes % 2 == 0) ? d_vals : U(L.tv1);
             uint32_t *thist = hist + 4 * kHistSlot;
-            emit_kernel<<<(unsigned)((N + kEmitTile - 1) / kEmitTile), 256, 0, s>>>(
-                t, P, (uint32_t)N, vin, sp.tiles, sp.rect, ek, ev, (uint32_t)capacity, hdr,
-                U(L.st_emit), plan, thist);
+            const unsigned eblocks = (unsigned)((N + kEmitTile - 1) / kEmitTile);
+            if (cfg->rect_mode == GS_RECT_ELLIPSE)
+                emit_kernel<true><<<eblocks, 256, 0, s>>>(t, P, (uint32_t)N, vin, sp.tiles, sp.rect, sp.rec,
+                                                          cfg->tile_w, cfg->tile_h, ek, ev, (uint32_t)capacity,
+                                                          hdr, U(L.st_emit), plan, thist);
+            else
+                emit_kernel<false><<<eblocks, 256, 0, s>>>(t, P, (uint32_t)N, vin, sp.tiles, sp.rect, sp.rec,
+                                                           cfg->tile_w, cfg->tile_h, ek, ev, (uint32_t)capacity,
+                                                           hdr, U(L.st_emit), plan, thist);
             count_launch();
             GS_LAUNCH_CHECK();
             // 4. tile sort

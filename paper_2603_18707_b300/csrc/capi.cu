@@ -27,7 +27,9 @@ bool build_cfg(const gs_config *cfg, CfgDev *d)
     if (!(cfg->t_min > 0.f && cfg->t_min < 1.f)) return false;
     if (!(cfg->aa_dilation >= 0.f) || !std::isfinite(cfg->aa_dilation)) return false;
     if (!valid_tile(cfg)) return false;
-    if (cfg->rect_mode != GS_RECT_AABB && cfg->rect_mode != GS_RECT_CIRCLE) return false;
+    if (cfg->rect_mode != GS_RECT_AABB && cfg->rect_mode != GS_RECT_CIRCLE &&
+        cfg->rect_mode != GS_RECT_ELLIPSE)
+        return false;
     for (int i = 0; i < 4; ++i)
         if (!std::isfinite(cfg->c[i])) return false;
     d->kind = cfg->kind;

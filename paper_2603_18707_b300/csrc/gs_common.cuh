@@ -187,6 +187,42 @@ __host__ __device__ inline float first_root_f32(const float c[4], int order, flo
     return x > 0.f ? x : INF;
 }
 
+// Tile columns [c0, c1] (within [cx0, cx1]) of tile row `ty` that hold a
+// pixel centre inside the ellipse A dx^2 + 2 B dx dy + C dy^2 <= xc around
+// (mx, my); false if none. Over the row's band of pixel-centre y values the
+// ellipse's x-extent is reached either at its own extreme points (dy =
+// +-Sxy sqrt(xc / Sxx), Sigma = conic^-1) or at a band edge; the pixel
+// columns whose centres fall inside it are mapped to tiles. Preprocessing
+// (to count) and emission (to write) call this with the same stored record
+// values, so both see the same set.
+__device__ __forceinline__ bool row_cols(float mx, float my, float A, float B, float C, float xc,
+                                         int ty, int tile_w, int tile_h, int W, int H, int cx0,
+                                         int cx1, int &c0, int &c1)
+{
+    const float det = A * C - B * B;
+    if (!(det > 0.f) || !(A > 0.f) || !(xc >= 0.f)) return false;
+    const float idet = 1.f / det;
+    const float Sxx = C * idet, Syy = A * idet, Sxy = -B * idet;
+    const float hy = sqrtf(xc * Syy);
+    const float ya = fmaxf(ty * tile_h + 0.5f, my - hy);
+    const float yb = fminf((float)min((ty + 1) * tile_h, H) - 0.5f, my + hy);
+    if (!(ya <= yb)) return false;
+    const float hx = sqrtf(xc * Sxx);
+    const float dys = Sxy * sqrtf(xc / Sxx);
+    const float dya = ya - my, dyb = yb - my;
+    const float iA = 1.f / A;
+    const float wa = sqrtf(fmaxf(A * xc - det * dya * dya, 0.f)) * iA;
+    const float wb = sqrtf(fmaxf(A * xc - det * dyb * dyb, 0.f)) * iA;
+    const float ca = -B * dya * iA, cb = -B * dyb * iA;
+    const float xmax = (dys >= dya && dys <= dyb) ? mx + hx : mx + fmaxf(ca + wa, cb + wb);
+    const float xmin = (-dys >= dya && -dys <= dyb) ? mx - hx : mx + fminf(ca - wa, cb - wb);
+    const float p0 = fmaxf(ceilf(xmin - 0.5f), 0.f), p1 = fminf(floorf(xmax - 0.5f), (float)(W - 1));
+    if (!(p0 <= p1)) return false;
+    c0 = max((int)p0 / tile_w, cx0);
+    c1 = min((int)p1 / tile_w, cx1);
+    return c0 <= c1;
+}
+
 } // namespace gs
 
 #define GS_LAUNCH_CHECK()                                        \

@@ -195,14 +195,24 @@ preprocess_kernel(const __grid_constant__ CamTable cams, const __grid_constant__
                     const float px1 = fminf(floorf(mx2 + hx - 0.5f), (float)(cm.W - 1));
                     const float py0 = fmaxf(ceilf(my2 - hy - 0.5f), 0.f);
                     const float py1 = fminf(floorf(my2 + hy - 0.5f), (float)(cm.H - 1));
+                    r0 = make_float4(mx2, my2, o2, tz);
+                    r1 = make_float4(cc * idet, -b * idet, a * idet, xc);
                     if (px0 <= px1 && py0 <= py1) {
                         const int gx0 = (int)px0 / cfg.tile_w, gx1 = (int)px1 / cfg.tile_w;
                         const int gy0 = (int)py0 / cfg.tile_h, gy1 = (int)py1 / cfg.tile_h;
                         rect = make_ushort4(gx0, gy0, gx1, gy1);
-                        ntiles = (uint32_t)((gx1 - gx0 + 1) * (gy1 - gy0 + 1));
+                        if (cfg.rect_mode == GS_RECT_ELLIPSE) {
+                            // only the tiles of each row that the ellipse reaches
+                            for (int ty = gy0; ty <= gy1; ++ty) {
+                                int c0, c1;
+                                if (row_cols(r0.x, r0.y, r1.x, r1.y, r1.z, r1.w, ty, cfg.tile_w,
+                                             cfg.tile_h, cm.W, cm.H, gx0, gx1, c0, c1))
+                                    ntiles += (uint32_t)(c1 - c0 + 1);
+                            }
+                        } else {
+                            ntiles = (uint32_t)((gx1 - gx0 + 1) * (gy1 - gy0 + 1));
+                        }
                     }
-                    r0 = make_float4(mx2, my2, o2, tz);
-                    r1 = make_float4(cc * idet, -b * idet, a * idet, xc);
                     r2 = make_float4(col[0], col[1], col[2], rho);
                 }
             }

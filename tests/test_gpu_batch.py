@@ -109,7 +109,7 @@ def test_autotuner_picks_a_measured_candidate_and_caches(gs, scene, tmp_path):
     r1 = autotune.autotune(cams, "poly1", "opacity", sc, 200_000, steps=2, cache=cache)
     assert tuple(r1["tile"]) in autotune.TILES and r1["px_per_thread"] in autotune.PPTS
     assert r1["batch"] in autotune.BATCHES
-    assert r1["ms"] == min(r1["trials_ms"].values())
+    assert r1["ms"] == min(v for v in r1["trials_ms"].values() if v is not None)
     assert len(r1["trials_ms"]) == len(autotune.TILES) * len(autotune.PPTS) + len(autotune.BATCHES) - 1
     r2 = autotune.autotune(cams, "poly1", "opacity", sc, 200_000, steps=2, cache=cache)
     assert r2 == r1
