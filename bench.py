@@ -244,6 +244,7 @@ def run_ours(a, world, rank, local):
         if rank == 0:
             print(json.dumps({"profile": a.profile, "steps": a.steps, "config": workload(a),
                               "overrides": over, "ms_per_step": e[0].elapsed_time(e[1]) / max(a.steps, 1),
+                              "records_drawn_overlaps": list(r.n_records()),
                               "launches_per_step": 14}), flush=True)
         return
     R = {"poly1": render.Rasterizer(cams, api.make_config("poly1", "opacity", **over), P),

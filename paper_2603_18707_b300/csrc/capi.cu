@@ -51,6 +51,14 @@ bool build_cfg(const gs_config *cfg, CfgDev *d)
         // the polynomial must start positive and reach zero (Sec. 3.2)
         if (!(cfg->c[0] > 0.f) || !(d->x0 < INFINITY)) return false;
     }
+    // Is k non-increasing on [0, x0]? (exp always; f1 iff c1 < 0; the
+    // others are checked on a grid.) The blend may then skip an entry for a
+    // whole pixel run from a lower bound of Q.
+    d->monotone = 1;
+    if (n == 1) d->monotone = cfg->c[1] < 0.f;
+    if (n >= 2)
+        for (int i = 0; i <= 1024; ++i)
+            if (poly_deriv_eval(cfg->c, n, d->x0 * i / 1024.f) > 1e-6f) d->monotone = 0;
     return true;
 }
 

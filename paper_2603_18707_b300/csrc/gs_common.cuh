@@ -46,6 +46,7 @@ struct CfgDev {
     float x0;   // first positive root of the polynomial (poly kinds), +inf for exp
     int batch;
     int ppt;    // pixels per thread
+    int monotone; // kernel non-increasing in Q over its support (allows skipping by Q bounds)
 };
 
 // Pointers into the record buffer (see gs_splat2d_bytes).

@@ -102,6 +102,8 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
     }
     const float eps = cfg.eps, amax = cfg.alpha_max, tmin = cfg.t_min;
     const __half2 x0h = __float2half2_rn(fminf(cfg.x0, 60000.f)), amaxh = __float2half2_rn(amax);
+    // the FP16x2 alphas carry ~1e-3 absolute error: skip only far below eps
+    const float eps_skip = HALF ? 0.5f * eps : eps * (1.f - 1.f / 1024.f);
     for (uint32_t base = 0; base < n; base += B) {
         if (__syncthreads_count(active != 0) == 0) break;
         for (int i = threadIdx.x; i < B; i += nthreads) {
@@ -129,6 +131,16 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
             const float vv = fmaf(a.w, y, b.x);
             const float v2 = vv * vv;
             const float p3 = (KIND == GS_K_POLY3) ? s_c[j].w : 0.f; // the cubic's top coefficient
+            if (PPT > 1 && cfg.monotone) {
+                // smallest Q over this thread's run of pixels: v^2 if u changes
+                // sign along the run, else at the end with the smaller |u|.
+                // With k non-increasing, alpha there bounds every pixel's; the
+                // skip threshold sits below eps so that rounding can never
+                // skip an entry that a pixel would take.
+                const float ua = fmaf(a.x, xs[0], ub), uz = fmaf(a.x, xs[PPT - 1], ub);
+                const float um = ((ua > 0.f) != (uz > 0.f)) ? 0.f : fminf(fabsf(ua), fabsf(uz));
+                if (alpha_of_q<KIND>(cfg, b, p3, fmaf(um, um, v2)) < eps_skip) continue;
+            }
             float al[PPT];
             bool any = false;
             if (HALF) {
@@ -146,9 +158,11 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
             } else {
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
+                    // min(alpha_max, x) < eps exactly when x < eps: the clamp
+                    // is applied only to entries that are blended
                     const float u = fmaf(a.x, xs[k], ub);
                     const float Q = fmaf(u, u, v2);
-                    al[k] = fminf(amax, alpha_of_q<KIND>(cfg, b, p3, Q));
+                    al[k] = alpha_of_q<KIND>(cfg, b, p3, Q);
                     any |= (active >> k & 1u) && al[k] >= eps;
                 }
             }
@@ -158,6 +172,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 if (!(active >> k & 1u) || !(al[k] >= eps)) continue;
+                al[k] = fminf(amax, al[k]);
                 const float Tn = fmaf(-al[k], T[k], T[k]);
                 if (Tn < tmin) {
                     active &= ~(1u << k);
