@@ -104,7 +104,9 @@ typedef struct {
     int32_t aa_normalize; /* 1: o' = o sqrt(|Sigma'| / |Sigma' + v I|) (Sec. 3.4) */
     float aa_dilation;    /* v added to the 2D covariance diagonal, 0.3 */
     int32_t tile_w;       /* tile width in pixels: 8, 16 or 32 */
-    int32_t tile_h;       /* tile height in pixels: 8 or 16 */
+    int32_t tile_h;       /* tile height in pixels: 8, 16 or 32; at most 512 pixels per
+                             tile, and at most 256 threads (tile pixels / px_per_thread)
+                             in the blend; the reverse pass needs tiles of <= 256 pixels */
     int32_t rect_mode;    /* gs_rect_mode */
     int32_t batch;        /* splats staged in shared memory per round: 32..256 */
     int32_t px_per_thread;/* pixels per thread in the blend: 1, 2 or 4 */

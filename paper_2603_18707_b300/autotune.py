@@ -21,7 +21,7 @@ import torch
 from . import api
 from .render import Rasterizer
 
-TILES = ((16, 16), (8, 8), (32, 8))
+TILES = ((16, 16), (8, 8), (32, 8), (32, 16))
 BATCHES = (256, 128, 64, 32)
 PPTS = (1, 2, 4)
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "gs_b300_autotune.json")

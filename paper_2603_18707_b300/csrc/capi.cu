@@ -14,7 +14,7 @@ void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxe
 static bool valid_tile(const gs_config *cfg)
 {
     const int w = cfg->tile_w, h = cfg->tile_h;
-    return (w == 8 || w == 16 || w == 32) && (h == 8 || h == 16) && w * h <= 256;
+    return (w == 8 || w == 16 || w == 32) && (h == 8 || h == 16 || h == 32) && w * h <= 512;
 }
 
 bool build_cfg(const gs_config *cfg, CfgDev *d)

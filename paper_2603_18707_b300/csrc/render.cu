@@ -294,6 +294,7 @@ extern "C" gs_status gs_render(void *stream, const gs_camera *cams, int32_t ncam
     if (half && ppt == 1) return GS_ERR_ARG; // packed pairs need 2 or 4 pixels per thread
     if (cfg->tile_w % ppt) return GS_ERR_ARG;
     const int threads = cfg->tile_w * cfg->tile_h / ppt;
+    if (threads > 256) return GS_ERR_ARG; // 512-pixel tiles need 2 or 4 pixels per thread
     if (t.total_tiles == 0) return GS_OK;
     RenderArgs g;
     g.rec = P > 0 ? splat2d_const(d_splat2d, (int64_t)ncam * P).rec : nullptr;

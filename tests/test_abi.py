@@ -97,7 +97,7 @@ def test_host_argument_checks(L):
                             C.c_void_p(260)) == GS_ERR_ARG
     # bad config fields
     for field, val in (("kind", 7), ("cull", 5), ("eps", 0.0), ("alpha_max", 1.5), ("tile_w", 12),
-                       ("tile_h", 32), ("t_min", -1.0)):
+                       ("tile_h", 64), ("t_min", -1.0)):
         bad = api.make_config("poly1", "opacity")
         setattr(bad, field, val)
         assert lb.gs_preprocess(None, cams, 1, 10, ptr, ptr, ptr, ptr, ptr, 0, C.byref(bad), ptr) == GS_ERR_ARG
