@@ -201,8 +201,10 @@ preprocess_kernel(const __grid_constant__ CamTable cams, const __grid_constant__
                         const int gx0 = (int)px0 / cfg.tile_w, gx1 = (int)px1 / cfg.tile_w;
                         const int gy0 = (int)py0 / cfg.tile_h, gy1 = (int)py1 / cfg.tile_h;
                         rect = make_ushort4(gx0, gy0, gx1, gy1);
-                        if (cfg.rect_mode == GS_RECT_ELLIPSE) {
-                            // only the tiles of each row that the ellipse reaches
+                        if (cfg.rect_mode == GS_RECT_ELLIPSE && gx1 > gx0 && gy1 > gy0) {
+                            // only the tiles of each row that the ellipse reaches (a
+                            // single-row or single-column rectangle keeps all its
+                            // tiles: the band covers the whole ellipse there)
                             for (int ty = gy0; ty <= gy1; ++ty) {
                                 int c0, c1;
                                 if (row_cols(r0.x, r0.y, r1.x, r1.y, r1.z, r1.w, ty, cfg.tile_w,

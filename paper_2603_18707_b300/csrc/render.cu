@@ -203,7 +203,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
 }
 
 template <int KIND, int PPT, bool HALF>
-__global__ void __launch_bounds__(256 / PPT)
+__global__ void __launch_bounds__(256)
 render_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
               const __grid_constant__ RenderArgs g)
 {
@@ -215,7 +215,7 @@ render_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ Cfg
 }
 
 template <int KIND, int PPT, bool HALF>
-__global__ void __launch_bounds__(256 / PPT)
+__global__ void __launch_bounds__(256)
 render_persistent_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
                          const __grid_constant__ RenderArgs g, uint32_t *work)
 {
