@@ -528,7 +528,8 @@ emit_kernel(const __grid_constant__ CamTable cams, int P, uint32_t n_records,
             const uint32_t l = pq - ebeg;
             const uint32_t row = l / erw, col = l - row * erw;
             bool keep = p < c_total;
-            if (ELL && keep && __shfl_sync(0xffffffffu, shape, e)) {
+            const uint32_t eshape = __shfl_sync(0xffffffffu, shape, e); // every lane shuffles
+            if (ELL && keep && eshape) {
                 const float4 g0 = rec[3 * (size_t)ev], g1 = rec[3 * (size_t)ev + 1];
                 const ushort4 rr = rects[ev];
                 const CamDev &cm = cams.cam[ev / (uint32_t)P];
