@@ -40,15 +40,28 @@ constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagIncl = 2u << 30;
 constexpr int kSpinLimit = 1 << 20;
 
+// Launch-shape constants (compile-time; -D overrides for tuning builds).
+#ifndef GS_SORT_ITEMS
+#define GS_SORT_ITEMS 16
+#endif
+#ifndef GS_SORT_MIN_BLOCKS
+#define GS_SORT_MIN_BLOCKS 4
+#endif
+#ifndef GS_LOOK_WINDOW
+#define GS_LOOK_WINDOW 4
+#endif
+#ifndef GS_EMIT_ITEMS
+#define GS_EMIT_ITEMS 8
+#endif
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
+constexpr int kSortItems = GS_SORT_ITEMS;
 constexpr int kSortTile = kSortThreads * kSortItems; // keys per partition
 constexpr int kCompactVec = 8;                       // uint4 loads per lane
 constexpr int kCompactTile = 256 * 4 * kCompactVec;  // 8192 records per partition
-constexpr int kEmitItems = 8;
-constexpr int kEmitTile = 256 * kEmitItems;          // 2048 records per partition
+constexpr int kEmitItems = GS_EMIT_ITEMS;
+constexpr int kEmitTile = 256 * kEmitItems;          // records per partition
 constexpr int kHistSlot = 512;                       // histogram entries per pass
-constexpr int kLookWindow = 4;
+constexpr int kLookWindow = GS_LOOK_WINDOW;
 
 enum Counter {
     CTR_COMPACT = 0,
@@ -285,7 +298,7 @@ constexpr size_t onesweep_smem()
 }
 
 template <int BITS>
-__global__ void __launch_bounds__(kSortThreads, 4) // 4 CTAs per SM: the pass is latency-bound
+__global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) // the pass is latency-bound
 onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                 uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
                 const uint32_t *n_ptr, int shift, const uint32_t *__restrict__ hist,
@@ -491,33 +504,89 @@ emit_kernel(const __grid_constant__ CamTable cams, int P, uint32_t n_records,
     }
     __syncthreads();
     const uint32_t part_excl = s_excl;
-    const uint32_t lt = lanemask_lt();
+    if (ELL) {
+        // two levels: the warp expands its records into tile rows (32 rows at
+        // a time), each lane finds its row's tile columns, then the warp
+        // writes those rows' tiles 32 at a time
+#pragma unroll 1
+        for (int j = 0; j < kEmitItems; ++j) {
+            const uint32_t rows = cnt[j] ? (uint32_t)(rc[j].w - rc[j].y + 1) : 0u;
+            const uint32_t r_incl = warp_incl_scan(rows);
+            const uint32_t r_total = __shfl_sync(0xffffffffu, r_incl, 31);
+            const uint32_t out_base = part_excl + warp_excl + off[j];
+            uint32_t emitted = 0;
+            for (uint32_t rb = 0; rb < r_total; rb += 32) {
+                const uint32_t r = rb + lane;
+                const uint32_t rq = min(r, r_total - 1u);
+                int e = 0;
 #pragma unroll
-    for (int j = 0; j < kEmitItems; ++j) {
-        // candidates: every tile of the rectangle; survivors: the ones written
-        // (all candidates, or for ELL the tiles a multi-row, multi-column
-        // rectangle's ellipse reaches, by the test preprocessing counted with)
-        const uint32_t rw = (uint32_t)rc[j].z - rc[j].x + 1u;
-        const uint32_t rh = (uint32_t)rc[j].w - rc[j].y + 1u;
-        const uint32_t cand = cnt[j] ? (ELL ? rw * rh : cnt[j]) : 0u;
-        const uint32_t c_incl = ELL ? warp_incl_scan(cand) : incl[j];
-        const uint32_t c_total = __shfl_sync(0xffffffffu, c_incl, 31);
+                for (int sft = 16; sft > 0; sft >>= 1) {
+                    const uint32_t c = __shfl_sync(0xffffffffu, r_incl, e + sft - 1);
+                    if (c <= rq) e += sft;
+                }
+                const uint32_t ev = __shfl_sync(0xffffffffu, v[j], e);
+                const uint32_t rexcl = __shfl_sync(0xffffffffu, r_incl - rows, e);
+                uint32_t cnt2 = 0, kb = 0;
+                if (r < r_total) {
+                    const float4 g0 = rec[3 * (size_t)ev], g1 = rec[3 * (size_t)ev + 1];
+                    const ushort4 rr = rects[ev];
+                    const CamDev &cm = cams.cam[ev / (uint32_t)P];
+                    const int ty = (int)rr.y + (int)(rq - rexcl);
+                    int c0 = rr.x, c1 = rr.z;
+                    // a single-row or single-column rectangle keeps all its tiles
+                    const bool simple = rr.z == rr.x || rr.w == rr.y;
+                    if (simple || row_cols(g0.x, g0.y, g1.x, g1.y, g1.z, g1.w, ty, tile_w, tile_h, cm.W,
+                                           cm.H, rr.x, rr.z, c0, c1)) {
+                        cnt2 = (uint32_t)(c1 - c0 + 1);
+                        kb = (uint32_t)cm.tile_base + (uint32_t)ty * cm.tiles_x + (uint32_t)c0;
+                    }
+                }
+                const uint32_t c_incl = warp_incl_scan(cnt2);
+                const uint32_t seg = __shfl_sync(0xffffffffu, c_incl, 31);
+                for (uint32_t b2 = 0; b2 < seg; b2 += 32) {
+                    const uint32_t p = b2 + lane;
+                    const uint32_t pq = min(p, seg - 1u);
+                    int f = 0;
+#pragma unroll
+                    for (int sft = 16; sft > 0; sft >>= 1) {
+                        const uint32_t c = __shfl_sync(0xffffffffu, c_incl, f + sft - 1);
+                        if (c <= pq) f += sft;
+                    }
+                    const uint32_t fkb = __shfl_sync(0xffffffffu, kb, f);
+                    const uint32_t fbeg = __shfl_sync(0xffffffffu, c_incl - cnt2, f);
+                    const uint32_t fv = __shfl_sync(0xffffffffu, ev, f);
+                    const uint32_t o = out_base + emitted + p;
+                    if (p < seg && o < capacity) {
+                        const uint32_t key = fkb + (pq - fbeg);
+                        keys_out[o] = key;
+                        vals_out[o] = fv;
+                        for (int q = 0; q < plan.passes; ++q)
+                            atomicAdd(&s_h[q][(key >> plan.shift[q]) & ((1u << plan.bits[q]) - 1u)], 1u);
+                    }
+                }
+                emitted += seg;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < (ELL ? 0 : kEmitItems); ++j) {
+        const uint32_t w_incl = incl[j];
+        const uint32_t w_total = __shfl_sync(0xffffffffu, w_incl, 31);
         const uint32_t out_base = part_excl + warp_excl + off[j];
         const int cam = (int)(v[j] / (uint32_t)P);
         const int tiles_x = cams.cam[cam].tiles_x;
         const uint32_t tbase = (uint32_t)cams.cam[cam].tile_base + (uint32_t)rc[j].y * tiles_x + rc[j].x;
-        const uint32_t beg = c_incl - cand;
-        const uint32_t shape = (rw > 1u && rh > 1u) ? 1u : 0u; // tested under ELL
-        uint32_t emitted = 0;
-        // the warp walks these candidates 32 at a time; every lane takes part
+        const uint32_t rw = (uint32_t)rc[j].z - rc[j].x + 1u;
+        const uint32_t beg = w_incl - cnt[j];
+        // the warp walks these overlaps 32 at a time; every lane takes part
         // in every shuffle, lanes past the end only skip the store
-        for (uint32_t b = 0; b < c_total; b += 32) {
+        for (uint32_t b = 0; b < w_total; b += 32) {
             const uint32_t p = b + lane;
-            const uint32_t pq = min(p, c_total - 1u);
+            const uint32_t pq = min(p, w_total - 1u);
             int e = 0; // owner lane: number of lanes whose inclusive prefix is <= pq
 #pragma unroll
             for (int sft = 16; sft > 0; sft >>= 1) {
-                const uint32_t c = __shfl_sync(0xffffffffu, c_incl, e + sft - 1);
+                const uint32_t c = __shfl_sync(0xffffffffu, w_incl, e + sft - 1);
                 if (c <= pq) e += sft;
             }
             const uint32_t ev = __shfl_sync(0xffffffffu, v[j], e);
@@ -527,27 +596,14 @@ emit_kernel(const __grid_constant__ CamTable cams, int P, uint32_t n_records,
             const uint32_t etx = __shfl_sync(0xffffffffu, (uint32_t)tiles_x, e);
             const uint32_t l = pq - ebeg;
             const uint32_t row = l / erw, col = l - row * erw;
-            bool keep = p < c_total;
-            const uint32_t eshape = __shfl_sync(0xffffffffu, shape, e); // every lane shuffles
-            if (ELL && keep && eshape) {
-                const float4 g0 = rec[3 * (size_t)ev], g1 = rec[3 * (size_t)ev + 1];
-                const ushort4 rr = rects[ev];
-                const CamDev &cm = cams.cam[ev / (uint32_t)P];
-                int c0, c1;
-                keep = row_cols(g0.x, g0.y, g1.x, g1.y, g1.z, g1.w, (int)rr.y + (int)row, tile_w, tile_h,
-                                cm.W, cm.H, rr.x, rr.z, c0, c1) &&
-                       (int)(rr.x + col) >= c0 && (int)(rr.x + col) <= c1;
-            }
-            const uint32_t m = __ballot_sync(0xffffffffu, keep);
-            const uint32_t o = out_base + emitted + __popc(m & lt);
-            if (keep && o < capacity) {
+            const uint32_t o = out_base + p;
+            if (p < w_total && o < capacity) {
                 const uint32_t key = etb + row * etx + col;
                 keys_out[o] = key;
                 vals_out[o] = ev;
                 for (int q = 0; q < plan.passes; ++q)
                     atomicAdd(&s_h[q][(key >> plan.shift[q]) & ((1u << plan.bits[q]) - 1u)], 1u);
             }
-            emitted += __popc(m);
         }
     }
     if (part == nparts - 1 && threadIdx.x == 0) {
