@@ -35,6 +35,29 @@ METRIC = "frames/s and Gsplat-evals/s, poly-1+opacity-cull vs exp on same B300 a
 # C += c a T (9).
 FLOP_PER_EVAL = {"poly1": 21, "exp": 20}
 SMS, FP32_LANES = 148, 128
+# DRAM bytes (read + write) of one f1 blend launch on this workload, from an
+# ncu capture of the current kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum); None until the current kernel has been captured.
+BLEND_TRAFFIC = None
+
+
+def fma_peak_tflops(half2: bool) -> float:
+    """Measured FFMA (or packed HFMA2) rate of this GPU in TFLOP/s: the
+    library's peak microbenchmark, 8 CTAs of 256 threads per SM, timed with
+    CUDA events over three launches after one warm-up launch."""
+    import torch
+    from paper_2603_18707_b300 import api
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    blocks = sms * 8
+    sink = torch.empty(blocks * 256, device="cuda", dtype=torch.float32)
+    api.gs_fma_peak(half2, blocks, 20, sink)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    flop = sum(api.gs_fma_peak(half2, blocks, 400, sink) for _ in range(3))
+    e1.record()
+    torch.cuda.synchronize()
+    return flop / (e0.elapsed_time(e1) / 1e3) / 1e12
 
 
 def parse():
@@ -335,12 +358,14 @@ def run_ours(a, world, rank, local):
     # roofline of the dominant kernel: the blend, bound by the FP32 pipes
     st = stages["poly1"]
     dom = max(st, key=st.get)
-    peak = SMS * FP32_LANES * 2 * 2032e6 / 1e12
+    peak_derived = SMS * FP32_LANES * 2 * 2032e6 / 1e12
+    peak = fma_peak_tflops(False)
     blend_s = st["blend_ms"] / 1e3
     achieved = evals["poly1"] * FLOP_PER_EVAL["poly1"] / blend_s / 1e12
     roofline = {"bound": "alu", "kernel": "blend (render_kernel<POLY1>)", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": "148 SMs x 128 FP32 lanes x 2 FLOP x 2032 MHz (derived)",
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": BLEND_TRAFFIC,
+                "peak_source": "measured FFMA rate (gs_fma_peak, this run); derived "
+                               f"148 SMs x 128 lanes x 2 FLOP x 2032 MHz = {peak_derived:.1f}",
                 "dominant_stage": dom}
 
     extra = {}

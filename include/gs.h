@@ -247,6 +247,20 @@ gs_status gs_bin_sort_noalloc(void *stream, const gs_camera *cams, int32_t ncam,
  * it. Returns GS_ERR_CUDA if the copy fails. */
 gs_status gs_workspace_status(void *stream, void *d_workspace, int32_t *code);
 
+/* Arithmetic peak microbenchmark (measurement helper, not part of the
+ * rendering path). The blend (gs_render) is bound by the FP32 FMA pipe, or
+ * by the packed FP16x2 pipe when fp16x2 is set, so its roofline denominator
+ * is the rate at which this GPU retires FFMA / HFMA2 lanes. Launches `blocks`
+ * CTAs of 256 threads; each thread runs 8 independent FMA chains for
+ * iters x 16 rounds (FP32 FFMA if half2 == 0, packed HFMA2 if half2 == 1) and
+ * writes one float to d_sink[blocks * 256] (device, caller-owned; the values
+ * are meaningless). *flop (host) receives the FLOP the launch performs
+ * (2 per FMA lane, 2 lanes per HFMA2); time the launch on `stream` with
+ * events. Returns GS_ERR_ARG for blocks <= 0, iters <= 0, a null pointer or
+ * half2 not 0/1, GS_ERR_CUDA if the launch fails. */
+gs_status gs_fma_peak(void *stream, int32_t half2, int32_t blocks, int32_t iters, float *d_sink,
+                      double *flop);
+
 /* Number of kernels this library has launched in this process (all entry
  * points), for launch accounting. */
 uint64_t gs_launch_count(void);

@@ -65,6 +65,7 @@ _SIGS = {
                                   C.POINTER(C.c_float), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                   _vp]),
     "gs_workspace_status": (_i32, [_vp, _vp, C.POINTER(_i32)]),
+    "gs_fma_peak": (_i32, [_vp, _i32, _i32, _i32, _vp, C.POINTER(C.c_double)]),
     "gs_launch_count": (C.c_uint64, []),
     "gs_status_string": (C.c_char_p, [_i32]),
 }

@@ -162,5 +162,14 @@ def gs_workspace_status(workspace, stream=None) -> int:
     return int(code.value)
 
 
+def gs_fma_peak(half2: bool, blocks: int, iters: int, sink, stream=None) -> float:
+    """Launches the FFMA (half2=False) or HFMA2 peak microbenchmark on the
+    stream; returns the FLOP it performs (time it with events)."""
+    flop = C.c_double(0.0)
+    check("gs_fma_peak", lib().gs_fma_peak(_stream(stream), int(bool(half2)), int(blocks), int(iters),
+                                           _p(sink), C.byref(flop)))
+    return float(flop.value)
+
+
 def gs_launch_count() -> int:
     return int(lib().gs_launch_count())

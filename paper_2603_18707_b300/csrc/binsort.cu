@@ -20,11 +20,11 @@
 // The depth digits are sorted once per record instead of once per overlap,
 // which moves far fewer bytes than sorting the 64-bit keys directly.
 //
-// Onesweep (one kernel per digit): each CTA claims the next partition of 4096
+// Onesweep (one kernel per digit): each CTA claims the next partition of 5120
 // keys from an atomic counter, ranks its keys per digit with warp
 // match/ballot, publishes per-digit counts and resolves its global offsets by
-// decoupled look-back over earlier partitions (four predecessors per load
-// round), then scatters through shared memory so that global stores are
+// decoupled look-back over earlier partitions (kLookWindow predecessors per
+// load round), then scatters through shared memory so that global stores are
 // contiguous per digit. Every spin-wait is bounded: on expiry it raises
 // GS_ERR_TIMEOUT in the workspace error word and carries on with what it has.
 #include <algorithm>
@@ -42,16 +42,16 @@ constexpr int kSpinLimit = 1 << 20;
 
 // Launch-shape constants (compile-time; -D overrides for tuning builds).
 #ifndef GS_SORT_ITEMS
-#define GS_SORT_ITEMS 16
+#define GS_SORT_ITEMS 20
 #endif
 #ifndef GS_SORT_MIN_BLOCKS
-#define GS_SORT_MIN_BLOCKS 4
+#define GS_SORT_MIN_BLOCKS 3
 #endif
 #ifndef GS_LOOK_WINDOW
-#define GS_LOOK_WINDOW 4
+#define GS_LOOK_WINDOW 1
 #endif
 #ifndef GS_EMIT_ITEMS
-#define GS_EMIT_ITEMS 8
+#define GS_EMIT_ITEMS 4
 #endif
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = GS_SORT_ITEMS;
@@ -325,7 +325,7 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
     const uint32_t nparts = (n + kSortTile - 1) / kSortTile;
     if (part >= nparts) return;
 
-    // warp-striped load: warp w owns keys [base + 512 w, base + 512 (w + 1))
+    // warp-striped load: warp w owns keys [base + 32 I w, base + 32 I (w + 1)), I = kSortItems
     const uint32_t wbase = part * kSortTile + warp * (32 * kSortItems);
     uint32_t k[kSortItems], v[kSortItems], r[kSortItems];
 #pragma unroll

@@ -125,4 +125,9 @@ def test_host_argument_checks(L):
                         None) == GS_ERR_ARG
     code = C.c_int32()
     assert lb.gs_workspace_status(None, None, C.byref(code)) == GS_ERR_ARG
+    flop = C.c_double()
+    assert lb.gs_fma_peak(None, 0, 0, 10, ptr, C.byref(flop)) == GS_ERR_ARG
+    assert lb.gs_fma_peak(None, 2, 1, 10, ptr, C.byref(flop)) == GS_ERR_ARG
+    assert lb.gs_fma_peak(None, 0, 1, 0, ptr, C.byref(flop)) == GS_ERR_ARG
+    assert lb.gs_fma_peak(None, 1, 1, 10, None, C.byref(flop)) == GS_ERR_ARG
     assert lb.gs_status_string(4) == b"overlap capacity exceeded"
