@@ -474,7 +474,7 @@ def bench_fp16x2(a):
         res = {}
         imgs = {}
         for half in (0, 1):
-            R = render.Rasterizer(cams, api.make_config(kind, "opacity", fp16x2=half, px_per_thread=2),
+            R = render.Rasterizer(cams, api.make_config(kind, "opacity", fp16x2=half, px_per_thread=4),
                                   a.splats)
             R.forward(sc, n_eval=False)
             imgs[half] = R.out.clone()

@@ -114,7 +114,8 @@ typedef struct {
     int32_t reserved[4];
 } gs_config;
 
-/* Fills a config with the defaults above for a kernel kind. f1 uses the
+/* Fills a config with the defaults above for a kernel kind (plus 16x16
+ * tiles, GS_RECT_AABB, batch 256, 4 pixels per thread, FP32). f1 uses the
  * paper's coefficients (Sec. 3.1, with the printed c0/c1 labels swapped:
  * c0 = 0.773, c1 = -0.773/4.386, root 4.386); f'2 and f3 use this library's
  * L1 fits by the Sec. 3.1 procedure (the paper does not print them). */

@@ -81,6 +81,30 @@ struct WsHeader {
 };
 
 // Digit plan of the tile-id sort.
+// Division of n < 2^31 by a fixed d >= 1 as a multiply-high and a shift:
+// with s = ceil(log2 d) and m = ceil(2^(31+s) / d) < 2^32, floor(n m / 2^(31+s))
+// = floor(n / d), since the error n (m - 2^(31+s)/d) / 2^(31+s) < n / 2^(31+s)
+// < 2^-s <= 1/d never carries past the next multiple of d.
+struct FastDiv {
+    uint32_t m;
+    int sh; // s - 1, or -1 for d == 1
+    static FastDiv make(uint32_t d)
+    {
+        FastDiv f;
+        if (d <= 1) {
+            f.m = 0;
+            f.sh = -1;
+            return f;
+        }
+        int s = 0;
+        while ((1ull << s) < d) ++s;
+        f.m = (uint32_t)(((1ull << (31 + s)) + d - 1) / d);
+        f.sh = s - 1;
+        return f;
+    }
+    __device__ __forceinline__ uint32_t div(uint32_t n) const { return sh < 0 ? n : __umulhi(n, m) >> sh; }
+};
+
 struct TilePlan {
     int passes;
     int bits[3];
@@ -146,6 +170,28 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x)
         if (lane >= o) x += y;
     }
     return x;
+}
+
+// Lanes of the warp whose BITS-bit digit equals this lane's: one ballot per
+// bit (GS_SORT_BALLOT, the default) or the match instruction.
+#ifndef GS_SORT_BALLOT
+#define GS_SORT_BALLOT 1
+#endif
+template <int BITS>
+__device__ __forceinline__ uint32_t warp_peers(uint32_t d)
+{
+#if GS_SORT_BALLOT
+    uint32_t m = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < BITS; ++b) {
+        const uint32_t bit = (d >> b) & 1u;
+        const uint32_t v = __ballot_sync(0xffffffffu, bit);
+        m &= bit ? v : ~v;
+    }
+    return m;
+#else
+    return __match_any_sync(0xffffffffu, d);
+#endif
 }
 
 __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b)
@@ -341,7 +387,7 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
         const uint32_t d = (k[j] >> shift) & M;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t peers = warp_peers<BITS>(d);
         const int leader = __ffs(peers) - 1;
         uint32_t old = 0;
         if (lane == leader) {
@@ -453,7 +499,7 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
 // (GS_RECT_ELLIPSE), else the whole rectangle.
 template <bool ELL>
 __global__ void __launch_bounds__(256)
-emit_kernel(const __grid_constant__ CamTable cams, int P, uint32_t n_records,
+emit_kernel(const __grid_constant__ CamTable cams, FastDiv pdiv, uint32_t n_records,
             const uint32_t *__restrict__ sorted_vals,
             const uint32_t *__restrict__ tiles, const ushort4 *__restrict__ rects,
             const float4 *__restrict__ rec, int tile_w, int tile_h,
@@ -462,7 +508,12 @@ emit_kernel(const __grid_constant__ CamTable cams, int P, uint32_t n_records,
 {
     __shared__ uint32_t s_part, s_excl, s_warp[8];
     __shared__ uint32_t s_h[3][kHistSlot];
+    __shared__ uint32_t s_tb[kMaxCams], s_tx[kMaxCams]; // per camera: first tile id, tiles per row
     for (int i = threadIdx.x; i < 3 * kHistSlot; i += 256) (&s_h[0][0])[i] = 0;
+    if (threadIdx.x < cams.ncam) {
+        s_tb[threadIdx.x] = (uint32_t)cams.cam[threadIdx.x].tile_base;
+        s_tx[threadIdx.x] = (uint32_t)cams.cam[threadIdx.x].tiles_x;
+    }
     if (threadIdx.x == 0) s_part = atomicAdd(&hdr->ctr[CTR_EMIT], 1u);
     __syncthreads();
     const uint32_t nv = hdr->n_vis;
@@ -530,7 +581,7 @@ emit_kernel(const __grid_constant__ CamTable cams, int P, uint32_t n_records,
                 if (r < r_total) {
                     const float4 g0 = rec[3 * (size_t)ev], g1 = rec[3 * (size_t)ev + 1];
                     const ushort4 rr = rects[ev];
-                    const CamDev &cm = cams.cam[ev / (uint32_t)P];
+                    const CamDev &cm = cams.cam[pdiv.div(ev)];
                     const int ty = (int)rr.y + (int)(rq - rexcl);
                     int c0 = rr.x, c1 = rr.z;
                     // a single-row or single-column rectangle keeps all its tiles
@@ -573,10 +624,11 @@ emit_kernel(const __grid_constant__ CamTable cams, int P, uint32_t n_records,
         const uint32_t w_incl = incl[j];
         const uint32_t w_total = __shfl_sync(0xffffffffu, w_incl, 31);
         const uint32_t out_base = part_excl + warp_excl + off[j];
-        const int cam = (int)(v[j] / (uint32_t)P);
-        const int tiles_x = cams.cam[cam].tiles_x;
-        const uint32_t tbase = (uint32_t)cams.cam[cam].tile_base + (uint32_t)rc[j].y * tiles_x + rc[j].x;
+        const uint32_t cam = pdiv.div(v[j]);
+        const uint32_t tiles_x = s_tx[cam];
+        const uint32_t tbase = s_tb[cam] + (uint32_t)rc[j].y * tiles_x + rc[j].x;
         const uint32_t rw = (uint32_t)rc[j].z - rc[j].x + 1u;
+        const float rrw = 1.f / (float)rw;
         const uint32_t beg = w_incl - cnt[j];
         // the warp walks these overlaps 32 at a time; every lane takes part
         // in every shuffle, lanes past the end only skip the store
@@ -593,9 +645,14 @@ emit_kernel(const __grid_constant__ CamTable cams, int P, uint32_t n_records,
             const uint32_t ebeg = __shfl_sync(0xffffffffu, beg, e);
             const uint32_t erw = __shfl_sync(0xffffffffu, rw, e);
             const uint32_t etb = __shfl_sync(0xffffffffu, tbase, e);
-            const uint32_t etx = __shfl_sync(0xffffffffu, (uint32_t)tiles_x, e);
+            const uint32_t etx = __shfl_sync(0xffffffffu, tiles_x, e);
+            const float errw = __shfl_sync(0xffffffffu, rrw, e);
             const uint32_t l = pq - ebeg;
-            const uint32_t row = l / erw, col = l - row * erw;
+            // l / erw from the reciprocal (l < 2^22: off by at most one), corrected
+            uint32_t row = (uint32_t)((float)l * errw);
+            row -= (row * erw > l) ? 1u : 0u;
+            row += ((row + 1u) * erw <= l) ? 1u : 0u;
+            const uint32_t col = l - row * erw;
             const uint32_t o = out_base + p;
             if (p < w_total && o < capacity) {
                 const uint32_t key = etb + row * etx + col;
@@ -619,21 +676,47 @@ emit_kernel(const __grid_constant__ CamTable cams, int P, uint32_t n_records,
     }
 }
 
-// 5. per-tile [start, end) and optional 64-bit keys.
+// 5. per-tile [start, end) and optional 64-bit keys. Each thread takes four
+// consecutive sorted keys (one 16-byte load); the neighbours across thread
+// boundaries come from the adjacent lanes, or from memory at warp edges.
 __global__ void __launch_bounds__(256)
 ranges_kernel(const uint32_t *__restrict__ tkeys, const uint32_t *__restrict__ vals,
               const uint32_t *__restrict__ dkey, const WsHeader *hdr, uint2 *__restrict__ ranges,
               unsigned long long *__restrict__ keys64, uint32_t total_tiles, uint32_t n_records)
 {
     const uint32_t n = hdr->n_over;
-    for (uint32_t i = blockIdx.x * 256 + threadIdx.x; i < n; i += gridDim.x * 256) {
-        const uint32_t t = tkeys[i];
-        if (t >= total_tiles) continue; // only after a timed-out wait
-        if (i == 0 || tkeys[i - 1] != t) ranges[t].x = i;
-        if (i + 1 == n || tkeys[i + 1] != t) ranges[t].y = i + 1;
-        if (keys64) {
-            const uint32_t v = vals[i];
-            keys64[i] = ((unsigned long long)t << 32) | (v < n_records ? dkey[v] : 0xffffffffu);
+    const uint32_t nq = (n + 3) / 4;
+    const int lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * 256;
+    // every lane of a warp runs the same number of rounds (full-mask shuffles)
+    for (uint32_t q0 = blockIdx.x * 256 + (threadIdx.x & ~31u); q0 < nq; q0 += stride) {
+        const uint32_t q = q0 + lane;
+        const uint32_t i0 = 4 * q;
+        uint32_t k[4];
+        if (i0 + 3 < n) {
+            const uint4 t = *reinterpret_cast<const uint4 *>(tkeys + i0);
+            k[0] = t.x, k[1] = t.y, k[2] = t.z, k[3] = t.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) k[e] = i0 + e < n ? tkeys[i0 + e] : 0xffffffffu;
+        }
+        uint32_t prev = __shfl_up_sync(0xffffffffu, k[3], 1);
+        uint32_t next = __shfl_down_sync(0xffffffffu, k[0], 1);
+        if (lane == 0) prev = (i0 > 0 && i0 - 1 < n) ? tkeys[i0 - 1] : 0xfffffffeu;
+        if (lane == 31) next = i0 + 4 < n ? tkeys[i0 + 4] : 0xfffffffeu;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const uint32_t i = i0 + e;
+            const uint32_t t = k[e];
+            if (i >= n || t >= total_tiles) continue; // t >= total_tiles only after a timed-out wait
+            const uint32_t before = e == 0 ? prev : k[e - 1];
+            const uint32_t after = e == 3 ? next : (i + 1 < n ? k[e + 1] : 0xfffffffeu);
+            if (i == 0 || before != t) ranges[t].x = i;
+            if (i + 1 == n || after != t) ranges[t].y = i + 1;
+            if (keys64) {
+                const uint32_t v = vals[i];
+                keys64[i] = ((unsigned long long)t << 32) | (v < n_records ? dkey[v] : 0xffffffffu);
+            }
         }
     }
 }
@@ -757,12 +840,13 @@ extern "C" gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t nc
             uint32_t *ev = (plan.passes % 2 == 0) ? d_vals : U(L.tv1);
             uint32_t *thist = hist + 4 * kHistSlot;
             const unsigned eblocks = (unsigned)((N + kEmitTile - 1) / kEmitTile);
+            const FastDiv pdiv = FastDiv::make((uint32_t)std::max(P, 1));
             if (cfg->rect_mode == GS_RECT_ELLIPSE)
-                emit_kernel<true><<<eblocks, 256, 0, s>>>(t, P, (uint32_t)N, vin, sp.tiles, sp.rect, sp.rec,
+                emit_kernel<true><<<eblocks, 256, 0, s>>>(t, pdiv, (uint32_t)N, vin, sp.tiles, sp.rect, sp.rec,
                                                           cfg->tile_w, cfg->tile_h, ek, ev, (uint32_t)capacity,
                                                           hdr, U(L.st_emit), plan, thist);
             else
-                emit_kernel<false><<<eblocks, 256, 0, s>>>(t, P, (uint32_t)N, vin, sp.tiles, sp.rect, sp.rec,
+                emit_kernel<false><<<eblocks, 256, 0, s>>>(t, pdiv, (uint32_t)N, vin, sp.tiles, sp.rect, sp.rec,
                                                            cfg->tile_w, cfg->tile_h, ek, ev, (uint32_t)capacity,
                                                            hdr, U(L.st_emit), plan, thist);
             count_launch();

@@ -99,7 +99,8 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
     const int nthreads = blockDim.x;
     const int B = cfg.batch;
 
-    float T[PPT], C0[PPT], C1[PPT], C2[PPT], xs[PPT];
+    const float eps = cfg.eps, amax = cfg.alpha_max, tmin = cfg.t_min;
+    float T[PPT], C0[PPT], C1[PPT], C2[PPT], xs[PPT], ek[PPT];
     uint32_t lastc[PPT], ne[PPT];
     unsigned active = 0;
 #pragma unroll
@@ -110,8 +111,10 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
         lastc[k] = 0;
         ne[k] = n;
         if (px0 + k < cm.W && py < cm.H) active |= 1u << k;
+        // the alpha a pixel takes: eps while it is active, never once it
+        // stopped (one compare per pixel and entry instead of a mask test)
+        ek[k] = (active >> k & 1u) ? eps : INFINITY;
     }
-    const float eps = cfg.eps, amax = cfg.alpha_max, tmin = cfg.t_min;
     const __half2 x0h = __float2half2_rn(fminf(cfg.x0, 60000.f)), amaxh = __float2half2_rn(amax);
     // the FP16x2 alphas carry ~1e-3 absolute error: skip only far below eps
     const float eps_skip = HALF ? 0.5f * eps : eps * (1.f - 1.f / 1024.f);
@@ -153,7 +156,6 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                 if (alpha_of_q<KIND>(cfg, b, p3, fmaf(um, um, v2)) < eps_skip) continue;
             }
             float al[PPT];
-            bool any = false;
             if (HALF) {
                 const uint4 hp = s_h[j];
                 const __half2 v2h = __float2half2_rn(v2);
@@ -164,8 +166,6 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                     al[k] = ap.x;
                     al[k + 1] = ap.y;
                 }
-#pragma unroll
-                for (int k = 0; k < PPT; ++k) any |= (active >> k & 1u) && al[k] >= eps;
             } else {
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
@@ -174,16 +174,14 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                     const float u = fmaf(a.x, xs[k], ub);
                     const float Q = fmaf(u, u, v2);
                     al[k] = alpha_of_q<KIND>(cfg, b, p3, Q);
-                    any |= (active >> k & 1u) && al[k] >= eps;
                 }
             }
-            if (!any) continue;
             const float4 col = s_c[j];
             const uint32_t pos = base + j + 1;
             if constexpr (blend_branchless<KIND>()) {
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    const bool use = (active >> k & 1u) && al[k] >= eps;
+                    const bool use = al[k] >= ek[k];
                     const float a = fminf(amax, al[k]);
                     const float Tn = fmaf(-a, T[k], T[k]);
                     const bool stop = use && Tn < tmin;
@@ -196,15 +194,17 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                     lastc[k] = add ? pos : lastc[k];
                     ne[k] = stop ? pos : ne[k];
                     active &= ~((unsigned)stop << k);
+                    ek[k] = stop ? INFINITY : ek[k];
                 }
             } else {
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    if (!(active >> k & 1u) || !(al[k] >= eps)) continue;
+                    if (!(al[k] >= ek[k])) continue;
                     al[k] = fminf(amax, al[k]);
                     const float Tn = fmaf(-al[k], T[k], T[k]);
                     if (Tn < tmin) {
                         active &= ~(1u << k);
+                        ek[k] = INFINITY;
                         ne[k] = pos;
                         continue;
                     }
