@@ -75,6 +75,7 @@ def parse():
     p.add_argument("--no-diff", action="store_true", help="skip the differentiable-render leg")
     p.add_argument("--no-batched", action="store_true", help="skip the 64-camera batched leg")
     p.add_argument("--no-fp16", action="store_true", help="skip the FP16x2 precision leg")
+    p.add_argument("--no-f2range", action="store_true", help="skip the range-extended f2 leg")
     p.add_argument("--ppt", type=int, default=None, help="pixels per blend thread (1, 2, 4)")
     p.add_argument("--tile", type=str, default=None, help="tile shape WxH, e.g. 16x16")
     p.add_argument("--rect", choices=["aabb", "circle", "ellipse"], default=None,
@@ -372,7 +373,8 @@ def run_ours(a, world, rank, local):
     del R, sc
     for name, on, fn in (("differentiable", not a.no_diff, bench_differentiable),
                          ("batched", not a.no_batched, bench_batched),
-                         ("fp16x2", not a.no_fp16, bench_fp16x2)):
+                         ("fp16x2", not a.no_fp16, bench_fp16x2),
+                         ("f2_range", not a.no_f2range, bench_f2_range)):
         if not on:
             continue
         torch.cuda.empty_cache()
@@ -491,6 +493,39 @@ def bench_fp16x2(a):
                                  "max_per_channel": [float(v) for v in err.max(0).values],
                                  "psnr_db": float(-10 * np.log10(max(mse, 1e-30))),
                                  "frac_px_above_2e-3": float((err.max(-1).values > 2e-3).double().mean())}}
+    return out
+
+
+def bench_f2_range(a):
+    """App. A on the headline workload: f2 fitted over the quadric range a
+    tile renderer evaluates, x_max(tile) (8 and 16 pixel tiles), rendered
+    with opacity culling; frames/s and PSNR against exp and against f1 on
+    the same frames."""
+    import numpy as np
+
+    from paper_2603_18707_b300 import api, render, synth
+    raw = synth.scene_clusters(a.splats, 0, sh_degree=3)
+    cams = synth.orbit_cameras(a.cams, a.width, a.height)
+    sc = render.activate(raw)
+    ref = {}
+    for kind in ("exp", "poly1"):
+        R = render.Rasterizer(cams, api.make_config(kind, "opacity"), a.splats)
+        R.forward(sc, n_eval=False)
+        ref[kind] = R.out.clone()
+        del R
+    out = {}
+    for tile, c in api.F2_RANGE.items():
+        R = render.Rasterizer(cams, api.make_config("poly2", "opacity", coeffs=c, tile=(tile, tile)), a.splats)
+        R.forward(sc, n_eval=False)
+        img = R.out.clone()
+        for _ in range(3):
+            R.run_async(sc)
+        ms = _events_ms(lambda: R.run_async(sc), max(5, a.steps // 6))
+        del R
+        psnr = {k: float(-10 * np.log10(max(float(((img.double() - v.double()) ** 2).mean()), 1e-30)))
+                for k, v in ref.items()}
+        out[f"tile{tile}"] = {"coeffs": list(c), "frames_per_s": a.cams / (ms / 1e3), "ms_per_step": ms,
+                              "psnr_db_vs_exp": psnr["exp"], "psnr_db_vs_poly1": psnr["poly1"]}
     return out
 
 

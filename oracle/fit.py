@@ -112,6 +112,70 @@ def fit(order: int, n: int = 1 << 14, steps: int = 20000, eps: float = EPS) -> n
     raise ValueError("order must be 1, 2 or 3")
 
 
+def x_max_tile(tile: float, eps: float = EPS, v: float = 0.3) -> float:
+    """App. A: the largest quadric a tile-culled renderer evaluates. A splat
+    with opacity 1 and smallest scale s_min = sqrt(v) (the floor the AA
+    dilation v puts on every scale) that barely touches a tile corner with its
+    eps cut-off, p_c = s_min sqrt(-2 ln eps) from its centre along the tile
+    diagonal, is still evaluated at the opposite corner, sqrt(2) p_t further:
+    x_max = ((p_c + sqrt(2) p_t) / s_min)^2."""
+    s_min = np.sqrt(v)
+    p_c = s_min * np.sqrt(-2.0 * np.log(eps))
+    return float(((p_c + np.sqrt(2.0) * tile) / s_min) ** 2)
+
+
+def range_samples(X: float, eps: float = EPS, n_core: int = 1 << 14, n_tail: int = 1 << 12):
+    """Midpoints and weights (interval width / X) of a grid on [0, X]: dense
+    on [0, -2 ln eps] where g is not negligible, coarse beyond. The weighted
+    sum is the same mean over x uniform on [0, X] as the uniform sampling of
+    Sec. 3.1, with fewer points where the integrand is flat."""
+    xe = min(x_max(eps), X)
+    a = (np.arange(n_core) + 0.5) / n_core * xe
+    wa = np.full(n_core, xe / n_core)
+    if X <= xe:
+        return a, wa / X
+    b = xe + (np.arange(n_tail) + 0.5) / n_tail * (X - xe)
+    wb = np.full(n_tail, (X - xe) / n_tail)
+    return np.concatenate([a, b]), np.concatenate([wa, wb]) / X
+
+
+def fit_f2_range(tile: float, steps: int = 20000, eps: float = EPS, v: float = 0.3) -> np.ndarray:
+    """App. A alternative to the cut of Eq. 6: f2(x) = max(c0 + c1 x + c2 x^2, 0)
+    (Eq. 2) fitted by the Sec. 3.1 L1 procedure over [0, x_max_tile(tile)]
+    instead of [0, -2 ln eps], so that the parabola does not rise above zero
+    again anywhere a tile-culled renderer evaluates it.
+
+    Reading: over [0, -2 ln eps] alone the L1 optimum has its two roots
+    together (the tangent parabola of the Eq. 6 fit, root 6.37), so over the
+    extended range the tail binds and the optimum puts the second root at
+    x_max exactly: f2(x) = c0 (1 - x / r) (1 - x / x_max) on [0, x_max]. The
+    fit is run over (c0, r) in that family (both well scaled), Adam on the
+    L1 subgradient as in fit()."""
+    X = x_max_tile(tile, eps, v)
+    x, w = range_samples(X, eps)
+    g = np.exp(-0.5 * x)
+    xe = x_max(eps)
+
+    def grad(p):
+        c0, z = p  # z = r / (-2 ln eps)
+        r = z * xe
+        a = 1.0 - x / r
+        b = 1.0 - x / X
+        f = c0 * a * b
+        s = np.sign(np.maximum(f, 0.0) - g) * (f > 0) * w
+        return np.array([np.sum(s * a * b), np.sum(s * c0 * b * x / (r * r) * xe)])
+
+    c0, z = _adam(grad, [0.773, 4.386 / xe], steps, 2e-2, 1e-6)
+    r = z * xe
+    return np.array([c0, -c0 * (1.0 / r + 1.0 / X), c0 / (r * X)])
+
+
+def roots_quadratic(c):
+    """Real roots of c0 + c1 x + c2 x^2, ascending (numpy)."""
+    r = np.roots([c[2], c[1], c[0]]) if c[2] != 0 else np.array([-c[0] / c[1]])
+    return np.sort(r[np.isreal(r)].real)
+
+
 if __name__ == "__main__":
     for N in (1, 2, 3):
         c = fit(N)

@@ -38,6 +38,15 @@ def camera_array(cams) -> C.Array:
     return arr
 
 
+# f2 = max(c0 + c1 x + c2 x^2, 0) fitted by the Sec. 3.1 L1 procedure over the
+# quadric range a tile renderer evaluates, [0, x_max(tile)] with
+# x_max = (sqrt(2) tile / sqrt(0.3) + sqrt(-2 ln(1/255)))^2 (App. A), per tile
+# size in pixels. The second root sits at x_max, so GS_K_POLY2 (cut at the
+# first root) renders it exactly: make_config("poly2", coeffs=F2_RANGE[16]).
+F2_RANGE = {8: (0.7706480720543922, -0.1763059655625171, 0.0003041422547261449),
+            16: (0.7700231846428013, -0.17549960677781712, 8.787264296324024e-05)}
+
+
 def make_config(kind="poly1", cull="opacity", **over) -> GsConfig:
     """Library defaults for a kernel kind and cull mode (gs_config_default),
     then field overrides, e.g. tile=(8, 8), coeffs=(...), aa=False."""

@@ -64,6 +64,8 @@ def test_default_coefficients_match_golden(L):
     for kind in ("poly1", "poly2", "poly3"):
         c = api.make_config(kind, "opacity")
         assert list(c.c) == pytest.approx(gold[kind], rel=1e-6, abs=1e-9)
+    for tile, c in api.F2_RANGE.items():
+        assert list(c) == pytest.approx(gold["poly2_range"][str(tile)][:3], rel=1e-12)
 
 
 def test_sizes_and_tiles(L):

@@ -130,6 +130,29 @@ def test_image_matches_oracle(gs, orc, small, kind, cull, ppt):
     assert np.abs(T - Tref)[far].max() < TOL_FP32
 
 
+@pytest.mark.parametrize("tile", [8, 16])
+@pytest.mark.parametrize("cull", ["universal", "opacity"])
+def test_f2_range_coefficients_match_oracle(gs, orc, small, tile, cull):
+    """App. A: f2 fitted over [0, x_max(tile)] renders through the quadratic
+    kernel (its second root lies past x_max, so the cut of Eq. 6 and
+    max(poly, 0) agree wherever the tile renderer evaluates it); GPU image vs
+    the untiled FP64 oracle with the same coefficients, at that tile size."""
+    from gpu_helpers import COEFFS
+    from paper_2603_18707_b300 import synth
+    c = tuple(COEFFS["poly2_range"][str(tile)][:3])
+    cam = synth.camera_small()
+    R = _gpu(gs, small, [cam], "poly2", cull, tile=(tile, tile), coeffs=c)
+    img = R.images()[0].cpu().numpy()
+    oc = orc.camera_from_dict(cam)
+    sc = orc.activate(small)
+    ref, _, _ = orc.render_untiled(sc, oc, orc.make_config("poly2", c, cull, tile=(tile, tile)))
+    *_, margin = orc.render_tiled(sc, oc, orc.make_config("poly2", c, "universal", tile=(tile, tile)),
+                                  with_margin=True)
+    worst, n_near, _ = _compare(img, ref, margin)
+    assert worst < TOL_FP32, (worst, n_near)
+    assert n_near < 0.01 * img.shape[0] * img.shape[1]
+
+
 def test_poly1_vs_exp_psnr_reported(gs, small):
     """Sec. 4.1 trend on the config-1 scene: f3 is closer to exp than f1."""
     from paper_2603_18707_b300 import synth
