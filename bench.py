@@ -35,10 +35,20 @@ METRIC = "frames/s and Gsplat-evals/s, poly-1+opacity-cull vs exp on same B300 a
 # C += c a T (9).
 FLOP_PER_EVAL = {"poly1": 21, "exp": 20}
 SMS, FP32_LANES = 148, 128
-# DRAM bytes (read + write) of one f1 blend launch on this workload, from an
-# ncu capture of the current kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum); None until the current kernel has been captured.
-BLEND_TRAFFIC = None
+# DRAM bytes (read + write) of one f1 blend launch (render_kernel<1, 4, 0>) on
+# the default workload (3M splats, 16 cameras at 1920x1080), from
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+#       --clock-control none -k regex:render_kernel -c 2
+#       python bench.py --profile poly1 --steps 2 --warmup 1
+# (1434055680 read + 641823232 written); set to None whenever the blend
+# kernel changes until it is captured again.
+BLEND_TRAFFIC = 1434055680 + 641823232
+
+
+def _default_workload(a) -> bool:
+    """The configuration BLEND_TRAFFIC was captured on."""
+    return ((a.splats, a.cams, a.width, a.height) == (3_000_000, 16, 1920, 1080)
+            and not a.tile and not a.ppt and not a.rect)
 
 
 def fma_peak_tflops(half2: bool) -> float:
@@ -364,7 +374,8 @@ def run_ours(a, world, rank, local):
     blend_s = st["blend_ms"] / 1e3
     achieved = evals["poly1"] * FLOP_PER_EVAL["poly1"] / blend_s / 1e12
     roofline = {"bound": "alu", "kernel": "blend (render_kernel<POLY1>)", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": BLEND_TRAFFIC,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": BLEND_TRAFFIC if _default_workload(a) else None,
                 "peak_source": "measured FFMA rate (gs_fma_peak, this run); derived "
                                f"148 SMs x 128 lanes x 2 FLOP x 2032 MHz = {peak_derived:.1f}",
                 "dominant_stage": dom}
