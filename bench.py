@@ -161,8 +161,9 @@ def dist_setup(a):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl" if a.impl == "ours" else "gloo")
+        dist.init_process_group("nccl" if a.impl == "ours" and torch.cuda.is_available() else "gloo")
     return world, rank, local
 
 
@@ -172,14 +173,25 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x: float, world: int) -> float:
+def _reduce(x: float, world: int, op: str) -> float:
+    """Host-side reduction of one timing or count over the ranks (not part of
+    the rendering path: the ranks exchange no data)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    return _reduce(x, world, "max")
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    return _reduce(x, world, "sum")
 
 
 # ---------------------------------------------------------------------------
@@ -254,7 +266,9 @@ def run_ours(a, world, rank, local):
     torch.cuda.set_device(local)
     _build.build()
     raw = synth.scene_clusters(a.splats, 0, sh_degree=3)
-    cams = synth.orbit_cameras(a.cams, a.width, a.height)
+    # each rank renders a.cams views of its own (interleaved on one orbit):
+    # the cameras are the units sharded across ranks, with no exchange
+    cams = synth.shard_orbit(a.cams, rank, world, a.width, a.height)
     sc = render.activate(raw)
     P = a.splats
     over = {}
@@ -402,6 +416,7 @@ def run_ours(a, world, rank, local):
         cpu = {"value": 1.0 / frame_s, "unit": "frames/s", "cores": os.cpu_count(),
                "kind": "oracle", "sample": desc + f" ({sample_s:.1f} s of CPU time)"}
 
+    evals_all = {k: sum_over_ranks(float(v), world) for k, v in evals.items()}
     if rank != 0:
         return
     ms = res["poly1"]
@@ -409,9 +424,9 @@ def run_ours(a, world, rank, local):
     line = {"metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload(a),
-            "gsplat_evals_per_s": world * evals["poly1"] / (ms / 1e3) / 1e9,
+            "gsplat_evals_per_s": evals_all["poly1"] / (ms / 1e3) / 1e9,
             "exp": {"frames_per_s": world * a.cams / (res["exp"] / 1e3), "ms_per_step": res["exp"],
-                    "gsplat_evals_per_s": world * evals["exp"] / (res["exp"] / 1e3) / 1e9},
+                    "gsplat_evals_per_s": evals_all["exp"] / (res["exp"] / 1e3) / 1e9},
             "speedup_poly1_vs_exp": res["exp"] / ms,
             "psnr_poly1_vs_exp_db": {"mean": float(np.mean(psnr)), "min": float(np.min(psnr))},
             "evals_per_step": evals, "overlaps_per_step": overlaps, "stages_ms": stages,

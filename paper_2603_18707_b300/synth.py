@@ -136,14 +136,22 @@ def camera_small(width: int = 128, height: int = 128) -> dict:
 
 
 def orbit_cameras(n: int, width: int = 1920, height: int = 1080, radius: float = 18.0,
-                  height_above: float = 2.0, fovx_deg: float = 60.0) -> list:
-    """n cameras evenly spaced on a horizontal orbit around the origin."""
+                  height_above: float = 2.0, fovx_deg: float = 60.0, phase: float = 0.0) -> list:
+    """n cameras evenly spaced on a horizontal orbit around the origin, the
+    k-th at angle 2 pi (k + phase) / n."""
     cams = []
     for k in range(n):
-        a = 2.0 * math.pi * k / n
+        a = 2.0 * math.pi * (k + phase) / n
         pos = [radius * math.sin(a), -height_above, -radius * math.cos(a)]
         cams.append(look_at(pos, [0.0, 0.0, 0.0], width, height, fovx_deg))
     return cams
+
+
+def shard_orbit(n: int, rank: int, world: int, width: int = 1920, height: int = 1080) -> list:
+    """Rank `rank` of `world`: n orbit cameras interleaved with the other
+    ranks' (phase rank / world), so that the ranks together render the
+    n * world views of one orbit and each rank as many as a single GPU."""
+    return orbit_cameras(n, width, height, phase=rank / world)
 
 
 def mixed_cameras(n: int = 64, radius: float = 18.0) -> list:
