@@ -248,6 +248,19 @@ gs_status gs_bin_sort_noalloc(void *stream, const gs_camera *cams, int32_t ncam,
  * it. Returns GS_ERR_CUDA if the copy fails. */
 gs_status gs_workspace_status(void *stream, void *d_workspace, int32_t *code);
 
+/* Self-test of the bounded waits (failure detection without a fault; not
+ * part of the rendering path). Runs one of the two decoupled look-back
+ * routines of gs_bin_sort against a predecessor partition that never
+ * publishes its count: which = 0 the scalar look-back (compaction, emission),
+ * which = 1 the per-digit look-back of a radix pass. The wait gives up after
+ * spin_limit short sleeps and ORs GS_ERR_TIMEOUT into the error word
+ * d_scratch[0]; the launch returns and the context stays usable.
+ * d_scratch: GS_SELFTEST_SCRATCH_BYTES of device memory (4-byte aligned),
+ * cleared by the call. Returns GS_ERR_ARG for a null pointer, which not 0/1,
+ * or spin_limit outside [1, 2^20]. */
+#define GS_SELFTEST_SCRATCH_BYTES 4096
+gs_status gs_selftest_lookback_timeout(void *stream, int32_t which, uint32_t *d_scratch, int32_t spin_limit);
+
 /* Arithmetic peak microbenchmark (measurement helper, not part of the
  * rendering path). The blend (gs_render) is bound by the FP32 FMA pipe, or
  * by the packed FP16x2 pipe when fp16x2 is set, so its roofline denominator

@@ -18,6 +18,7 @@ GS_K_EXP, GS_K_POLY1, GS_K_POLY2, GS_K_POLY3 = 0, 1, 2, 3
 GS_CULL_UNIVERSAL, GS_CULL_OPACITY, GS_CULL_LEGACY3 = 0, 1, 2
 GS_RECT_AABB, GS_RECT_CIRCLE, GS_RECT_ELLIPSE = 0, 1, 2
 GS_MAX_CAMERAS = 64
+GS_SELFTEST_SCRATCH_BYTES = 4096
 
 KIND = {"exp": GS_K_EXP, "poly1": GS_K_POLY1, "poly2": GS_K_POLY2, "poly3": GS_K_POLY3}
 CULL = {"universal": GS_CULL_UNIVERSAL, "opacity": GS_CULL_OPACITY, "legacy3": GS_CULL_LEGACY3}
@@ -66,6 +67,7 @@ _SIGS = {
                                   _vp]),
     "gs_workspace_status": (_i32, [_vp, _vp, C.POINTER(_i32)]),
     "gs_fma_peak": (_i32, [_vp, _i32, _i32, _i32, _vp, C.POINTER(C.c_double)]),
+    "gs_selftest_lookback_timeout": (_i32, [_vp, _i32, _vp, _i32]),
     "gs_launch_count": (C.c_uint64, []),
     "gs_status_string": (C.c_char_p, [_i32]),
 }

@@ -171,6 +171,15 @@ def gs_workspace_status(workspace, stream=None) -> int:
     return int(code.value)
 
 
+def gs_selftest_lookback_timeout(which: int, scratch, spin_limit: int, stream=None) -> None:
+    """Runs a look-back against a predecessor that never publishes (which 0:
+    scalar, 1: per digit); the error word scratch[0] then holds
+    GS_ERR_TIMEOUT. scratch: int32/uint32 device tensor of
+    GS_SELFTEST_SCRATCH_BYTES bytes."""
+    check("gs_selftest_lookback_timeout",
+          lib().gs_selftest_lookback_timeout(_stream(stream), int(which), _p(scratch), int(spin_limit)))
+
+
 def gs_fma_peak(half2: bool, blocks: int, iters: int, sink, stream=None) -> float:
     """Launches the FFMA (half2=False) or HFMA2 peak microbenchmark on the
     stream; returns the FLOP it performs (time it with events)."""

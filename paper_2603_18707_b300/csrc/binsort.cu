@@ -204,7 +204,8 @@ __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b)
 // this partition's aggregate, accumulates predecessors 32 at a time until an
 // inclusive prefix is found, publishes the inclusive prefix and returns the
 // exclusive one (same value in every lane).
-__device__ uint32_t lookback_scalar(uint32_t *state, uint32_t part, uint32_t agg, uint32_t *err)
+__device__ uint32_t lookback_scalar(uint32_t *state, uint32_t part, uint32_t agg, uint32_t *err,
+                                   int limit = kSpinLimit)
 {
     const int lane = threadIdx.x & 31;
     if (part == 0) {
@@ -219,7 +220,7 @@ __device__ uint32_t lookback_scalar(uint32_t *state, uint32_t part, uint32_t agg
         const int64_t idx = p - lane;
         uint32_t s = idx >= 0 ? ld_relaxed(&state[idx]) : kFlagIncl;
         while (__any_sync(0xffffffffu, (s >> 30) == 0)) {
-            if (++spins > kSpinLimit) {
+            if (++spins > limit) {
                 if (lane == 0) atomicOr(err, (uint32_t)GS_ERR_TIMEOUT);
                 if ((s >> 30) == 0) s = kFlagIncl;
                 break;
@@ -235,6 +236,50 @@ __device__ uint32_t lookback_scalar(uint32_t *state, uint32_t part, uint32_t agg
         p -= 32;
     }
     if (lane == 0) st_relaxed(&state[part], kFlagIncl | sat_add(excl, agg));
+    return excl;
+}
+
+// Decoupled look-back of one digit of a Onesweep pass (one thread per
+// digit): sums the published counts of this digit in the partitions before
+// `part` (kLookWindow per load round) until one with an inclusive prefix.
+// A predecessor that has published nothing is re-read after a short sleep,
+// at most `limit` times; then GS_ERR_TIMEOUT is raised and what was summed
+// is returned.
+__device__ uint32_t lookback_digit(const uint32_t *state, uint32_t part, int R, int d, uint32_t *err,
+                                   int limit)
+{
+    uint32_t excl = 0;
+    int64_t p = (int64_t)part - 1;
+    int spins = 0;
+    bool done = false;
+    while (!done && p >= 0) {
+        uint32_t s[kLookWindow];
+#pragma unroll
+        for (int w = 0; w < kLookWindow; ++w)
+            s[w] = (p - w >= 0) ? ld_relaxed(&state[(size_t)(p - w) * R + d]) : kFlagIncl;
+        int used = 0;
+        bool stall = false;
+#pragma unroll
+        for (int w = 0; w < kLookWindow; ++w) {
+            if (done || stall) continue;
+            const uint32_t f = s[w] >> 30;
+            if (f == 0) {
+                stall = true;
+                continue;
+            }
+            excl = sat_add(excl, s[w] & kValMask);
+            ++used;
+            if (f == 2) done = true;
+        }
+        p -= used;
+        if (stall && !done) {
+            if (++spins > limit) {
+                atomicOr(err, (uint32_t)GS_ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(32);
+        }
+    }
     return excl;
 }
 
@@ -435,38 +480,7 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
             st_relaxed(&st[d], kFlagIncl | agg);
         } else {
             st_relaxed(&st[d], kFlagAgg | agg);
-            // decoupled look-back, kLookWindow predecessors per load round
-            int64_t p = (int64_t)part - 1;
-            int spins = 0;
-            bool done = false;
-            while (!done && p >= 0) {
-                uint32_t s[kLookWindow];
-#pragma unroll
-                for (int w = 0; w < kLookWindow; ++w)
-                    s[w] = (p - w >= 0) ? ld_relaxed(&state[(size_t)(p - w) * R + d]) : kFlagIncl;
-                int used = 0;
-                bool stall = false;
-#pragma unroll
-                for (int w = 0; w < kLookWindow; ++w) {
-                    if (done || stall) continue;
-                    const uint32_t f = s[w] >> 30;
-                    if (f == 0) {
-                        stall = true;
-                        continue;
-                    }
-                    excl = sat_add(excl, s[w] & kValMask);
-                    ++used;
-                    if (f == 2) done = true;
-                }
-                p -= used;
-                if (stall && !done) {
-                    if (++spins > kSpinLimit) {
-                        atomicOr(err, (uint32_t)GS_ERR_TIMEOUT);
-                        break;
-                    }
-                    __nanosleep(32);
-                }
-            }
+            excl = lookback_digit(state, part, R, d, err, kSpinLimit);
             st_relaxed(&st[d], kFlagIncl | sat_add(excl, agg));
         }
         s_goff[d] = hex + excl;
@@ -900,5 +914,39 @@ extern "C" gs_status gs_workspace_status(void *stream, void *d_workspace, int32_
     if (cudaStreamSynchronize(s) != cudaSuccess) return GS_ERR_CUDA;
     if (cudaMemsetAsync(&hdr->err, 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
     *code = (int32_t)v;
+    return GS_OK;
+}
+
+// Self-test of the bounded waits (fault injection without a fault): the two
+// look-back routines above run against a predecessor that never publishes
+// (all-zero flags in d_scratch). They must give up after `limit` sleeps,
+// raise GS_ERR_TIMEOUT in the error word and return, leaving the context
+// usable.
+namespace gs {
+namespace {
+__global__ void lookback_selftest_kernel(int which, uint32_t *state, uint32_t *err, int limit)
+{
+    if (which == 0) {
+        if (threadIdx.x < 32) (void)lookback_scalar(state, 1u, 5u, err, limit);
+    } else {
+        (void)lookback_digit(state, 1u, 256, (int)threadIdx.x, err, limit);
+    }
+}
+} // namespace
+} // namespace gs
+
+extern "C" gs_status gs_selftest_lookback_timeout(void *stream, int32_t which, uint32_t *d_scratch,
+                                                  int32_t spin_limit)
+{
+    if (!d_scratch || (which != 0 && which != 1) || spin_limit < 1 || spin_limit > kSpinLimit) return GS_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // d_scratch: [0] error word, [64, 64 + 512) look-back flags of partitions 0 and 1
+    if (cudaMemsetAsync(d_scratch, 0, GS_SELFTEST_SCRATCH_BYTES, s) != cudaSuccess) return GS_ERR_CUDA;
+    lookback_selftest_kernel<<<1, which == 0 ? 32 : 256, 0, s>>>(which, d_scratch + 64, d_scratch, spin_limit);
+    count_launch();
+    if (cudaPeekAtLastError() != cudaSuccess) {
+        cudaGetLastError();
+        return GS_ERR_CUDA;
+    }
     return GS_OK;
 }

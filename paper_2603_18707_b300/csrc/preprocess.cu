@@ -79,8 +79,11 @@ __device__ __forceinline__ float support_threshold(const CfgDev &cfg, float o)
     return r;
 }
 
+#ifndef GS_PRE_MIN_BLOCKS
+#define GS_PRE_MIN_BLOCKS 1
+#endif
 template <int D>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, GS_PRE_MIN_BLOCKS)
 preprocess_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
                   int P, const float *__restrict__ means, const float *__restrict__ scales,
                   const float *__restrict__ quats, const float *__restrict__ opacities,

@@ -30,6 +30,9 @@ namespace gs {
 namespace {
 
 constexpr int kMaxBatch = 256;
+#ifndef GS_RENDER_MIN_BLOCKS
+#define GS_RENDER_MIN_BLOCKS 1 // CTAs of 256 threads per SM the register budget must allow
+#endif
 // Per-pixel update: predicated (no branch per pixel) or branching. 0: branch
 // for every kernel, 1: predicate for every kernel, 2: predicate for exp only
 // (measured: exp, which blends more entries per pixel, gains ~8%; f1 loses ~7%).
@@ -233,7 +236,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
 }
 
 template <int KIND, int PPT, bool HALF>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, GS_RENDER_MIN_BLOCKS)
 render_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
               const __grid_constant__ RenderArgs g)
 {
@@ -245,7 +248,7 @@ render_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ Cfg
 }
 
 template <int KIND, int PPT, bool HALF>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, GS_RENDER_MIN_BLOCKS)
 render_persistent_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
                          const __grid_constant__ RenderArgs g, uint32_t *work)
 {

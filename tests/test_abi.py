@@ -127,6 +127,10 @@ def test_host_argument_checks(L):
                         None) == GS_ERR_ARG
     code = C.c_int32()
     assert lb.gs_workspace_status(None, None, C.byref(code)) == GS_ERR_ARG
+    assert lb.gs_selftest_lookback_timeout(None, 0, None, 100) == GS_ERR_ARG
+    assert lb.gs_selftest_lookback_timeout(None, 2, ptr, 100) == GS_ERR_ARG
+    assert lb.gs_selftest_lookback_timeout(None, 1, ptr, 0) == GS_ERR_ARG
+    assert lb.gs_selftest_lookback_timeout(None, 1, ptr, (1 << 20) + 1) == GS_ERR_ARG
     flop = C.c_double()
     assert lb.gs_fma_peak(None, 0, 0, 10, ptr, C.byref(flop)) == GS_ERR_ARG
     assert lb.gs_fma_peak(None, 2, 1, 10, ptr, C.byref(flop)) == GS_ERR_ARG
