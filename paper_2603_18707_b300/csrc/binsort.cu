@@ -50,6 +50,14 @@ constexpr int kSpinLimit = 1 << 20;
 #ifndef GS_LOOK_WINDOW
 #define GS_LOOK_WINDOW 1
 #endif
+#ifndef GS_EMIT_MIN_BLOCKS
+#define GS_EMIT_MIN_BLOCKS 0 // 0: no register cap from the occupancy target
+#endif
+#if GS_EMIT_MIN_BLOCKS
+#define GS_EMIT_BOUNDS __launch_bounds__(256, GS_EMIT_MIN_BLOCKS)
+#else
+#define GS_EMIT_BOUNDS __launch_bounds__(256)
+#endif
 #ifndef GS_EMIT_ITEMS
 #define GS_EMIT_ITEMS 4
 #endif
@@ -512,7 +520,7 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
 // only the tiles of each rectangle row that the support ellipse reaches
 // (GS_RECT_ELLIPSE), else the whole rectangle.
 template <bool ELL>
-__global__ void __launch_bounds__(256)
+__global__ void GS_EMIT_BOUNDS
 emit_kernel(const __grid_constant__ CamTable cams, FastDiv pdiv, uint32_t n_records,
             const uint32_t *__restrict__ sorted_vals,
             const uint32_t *__restrict__ tiles, const ushort4 *__restrict__ rects,

@@ -31,7 +31,7 @@ namespace {
 
 constexpr int kMaxBatch = 256;
 #ifndef GS_RENDER_MIN_BLOCKS
-#define GS_RENDER_MIN_BLOCKS 1 // CTAs of 256 threads per SM the register budget must allow
+#define GS_RENDER_MIN_BLOCKS 4 // 256-thread CTAs per SM the register budget must allow (64 registers: measured fastest)
 #endif
 // Per-pixel update: predicated (no branch per pixel) or branching. 0: branch
 // for every kernel, 1: predicate for every kernel, 2: predicate for exp only
