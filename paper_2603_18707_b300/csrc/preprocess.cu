@@ -80,7 +80,7 @@ __device__ __forceinline__ float support_threshold(const CfgDev &cfg, float o)
 }
 
 #ifndef GS_PRE_MIN_BLOCKS
-#define GS_PRE_MIN_BLOCKS 5 // 128-thread CTAs per SM (96 registers: measured fastest)
+#define GS_PRE_MIN_BLOCKS 8 // 128-thread CTAs per SM the register budget must allow
 #endif
 template <int D>
 __global__ void __launch_bounds__(128, GS_PRE_MIN_BLOCKS)
@@ -89,26 +89,37 @@ preprocess_kernel(const __grid_constant__ CamTable cams, const __grid_constant__
                   const float *__restrict__ quats, const float *__restrict__ opacities,
                   const float *__restrict__ sh, Splat2DPtrs out)
 {
-    constexpr int K = (D + 1) * (D + 1);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int K = (D + 1) * (D + 1), F = 3 * K;
+    // the CTA's SH coefficients, transposed ([coefficient][splat]) so that a
+    // warp reading one coefficient of its 32 splats hits 32 banks; staged once
+    // and read for every camera (kept out of registers: higher occupancy)
+    __shared__ float s_sh[F * 128];
+    const int i0 = blockIdx.x * 128, i = i0 + (int)threadIdx.x;
+    const int nb = min(128, P - i0);
+    const float *src = sh + (size_t)i0 * F;
+    if (F % 4 == 0) {
+        for (int e = threadIdx.x; e < nb * F / 4; e += 128) {
+            const float4 v = reinterpret_cast<const float4 *>(src)[e];
+            const int sp = (4 * e) / F, j = 4 * e - sp * F; // the four floats share a splat
+            s_sh[(j + 0) * 128 + sp] = v.x;
+            s_sh[(j + 1) * 128 + sp] = v.y;
+            s_sh[(j + 2) * 128 + sp] = v.z;
+            s_sh[(j + 3) * 128 + sp] = v.w;
+        }
+    } else {
+        for (int e = threadIdx.x; e < nb * F; e += 128) {
+            const int sp = e / F;
+            s_sh[(e - sp * F) * 128 + sp] = src[e];
+        }
+    }
+    __syncthreads();
     if (i >= P) return;
+    const float *coef = s_sh + threadIdx.x; // coefficient j at coef[128 j]
 
     const float mx = means[3 * i + 0], my = means[3 * i + 1], mz = means[3 * i + 2];
     const float sx = scales[3 * i + 0], sy = scales[3 * i + 1], sz = scales[3 * i + 2];
     const float4 q4 = reinterpret_cast<const float4 *>(quats)[i];
     const float op = opacities[i];
-    float coef[K * 3];
-    if (K * 3 % 4 == 0) {
-        const float4 *s4 = reinterpret_cast<const float4 *>(sh + (size_t)i * K * 3);
-#pragma unroll
-        for (int k = 0; k < K * 3 / 4; ++k) {
-            float4 v = s4[k];
-            coef[4 * k + 0] = v.x; coef[4 * k + 1] = v.y; coef[4 * k + 2] = v.z; coef[4 * k + 3] = v.w;
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < K * 3; ++k) coef[k] = sh[(size_t)i * K * 3 + k];
-    }
 
     // Sigma = M M^T with M = R(q) diag(s), q normalised.
     const float qn = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
@@ -166,20 +177,6 @@ preprocess_kernel(const __grid_constant__ CamTable cams, const __grid_constant__
                 const float idet = 1.f / det1;
                 const float mx2 = cm.fx * tx * iz + cm.cx;
                 const float my2 = cm.fy * ty * iz + cm.cy;
-                // view-dependent colour
-                float dx = mx - cm.campos[0], dy = my - cm.campos[1], dz = mz - cm.campos[2];
-                const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
-                dx *= il; dy *= il; dz *= il;
-                float Y[K];
-                sh_basis<D>(dx, dy, dz, Y);
-                float col[3];
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    float acc = 0.f;
-#pragma unroll
-                    for (int k = 0; k < K; ++k) acc = fmaf(Y[k], coef[3 * k + ch], acc);
-                    col[ch] = fmaxf(acc + 0.5f, 0.f);
-                }
                 float xc = support_threshold(cfg, o2);
                 drawn = xc >= 0.f;
                 if (drawn) {
@@ -218,7 +215,23 @@ preprocess_kernel(const __grid_constant__ CamTable cams, const __grid_constant__
                             ntiles = (uint32_t)((gx1 - gx0 + 1) * (gy1 - gy0 + 1));
                         }
                     }
-                    r2 = make_float4(col[0], col[1], col[2], rho);
+                    if (ntiles) {
+                        // view-dependent colour, only for records that are drawn
+                        float dx = mx - cm.campos[0], dy = my - cm.campos[1], dz = mz - cm.campos[2];
+                        const float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+                        dx *= il; dy *= il; dz *= il;
+                        float Y[K];
+                        sh_basis<D>(dx, dy, dz, Y);
+                        float col[3];
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) {
+                            float acc = 0.f;
+#pragma unroll
+                            for (int k = 0; k < K; ++k) acc = fmaf(Y[k], coef[128 * (3 * k + ch)], acc);
+                            col[ch] = fmaxf(acc + 0.5f, 0.f);
+                        }
+                        r2 = make_float4(col[0], col[1], col[2], rho);
+                    }
                 }
             }
         }
