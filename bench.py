@@ -86,6 +86,7 @@ def parse():
     p.add_argument("--no-batched", action="store_true", help="skip the 64-camera batched leg")
     p.add_argument("--no-fp16", action="store_true", help="skip the FP16x2 precision leg")
     p.add_argument("--no-f2range", action="store_true", help="skip the range-extended f2 leg")
+    p.add_argument("--no-tensor", action="store_true", help="skip the tensor-core quadric leg")
     p.add_argument("--ppt", type=int, default=None, help="pixels per blend thread (1, 2, 4)")
     p.add_argument("--tile", type=str, default=None, help="tile shape WxH, e.g. 16x16")
     p.add_argument("--rect", choices=["aabb", "circle", "ellipse"], default=None,
@@ -399,7 +400,8 @@ def run_ours(a, world, rank, local):
     for name, on, fn in (("differentiable", not a.no_diff, bench_differentiable),
                          ("batched", not a.no_batched, bench_batched),
                          ("fp16x2", not a.no_fp16, bench_fp16x2),
-                         ("f2_range", not a.no_f2range, bench_f2_range)):
+                         ("f2_range", not a.no_f2range, bench_f2_range),
+                         ("tensor_quadric", not a.no_tensor, bench_tensor_quadric)):
         if not on:
             continue
         torch.cuda.empty_cache()
@@ -552,6 +554,33 @@ def bench_f2_range(a):
                 for k, v in ref.items()}
         out[f"tile{tile}"] = {"coeffs": list(c), "frames_per_s": a.cams / (ms / 1e3), "ms_per_step": ms,
                               "psnr_db_vs_exp": psnr["exp"], "psnr_db_vs_poly1": psnr["poly1"]}
+    return out
+
+
+def bench_tensor_quadric(a):
+    """Sec. 5.1 mapped onto the tensor cores, on the headline workload: the
+    quadric of every (pixel, splat) pair of a batch by mma.sync TF32 with
+    split weights (config tensor_alpha), against the FP32 blend: frames/s
+    and the largest per-channel difference of the images."""
+    from paper_2603_18707_b300 import api, render, synth
+    raw = synth.scene_clusters(a.splats, 0, sh_degree=3)
+    cams = synth.orbit_cameras(a.cams, a.width, a.height)
+    sc = render.activate(raw)
+    out = {}
+    for kind in ("poly1", "exp"):
+        res, imgs, blend = {}, {}, {}
+        for tc in (0, 1):
+            R = render.Rasterizer(cams, api.make_config(kind, "opacity", tensor_alpha=tc), a.splats)
+            R.forward(sc, n_eval=False)
+            imgs[tc] = R.out.clone()
+            for _ in range(3):
+                R.run_async(sc)
+            res[tc] = _events_ms(lambda: R.run_async(sc), max(5, a.steps // 6))
+            blend[tc] = _events_ms(lambda: R.blend(n_eval=False), max(5, a.steps // 6))
+            del R
+        out[kind] = {"frames_per_s_tensor": a.cams / (res[1] / 1e3), "frames_per_s_fp32": a.cams / (res[0] / 1e3),
+                     "blend_ms_tensor": blend[1], "blend_ms_fp32": blend[0],
+                     "max_abs_diff_vs_fp32": float((imgs[1] - imgs[0]).abs().max())}
     return out
 
 

@@ -111,7 +111,11 @@ typedef struct {
     int32_t batch;        /* splats staged in shared memory per round: 32..256 */
     int32_t px_per_thread;/* pixels per thread in the blend: 1, 2 or 4 */
     int32_t fp16x2;       /* 1: quadric and polynomial in packed FP16x2 */
-    int32_t reserved[4];
+    int32_t tensor_alpha; /* 1: quadric of every (pixel, splat) pair on the tensor cores
+                             (mma.sync TF32, weights split in two TF32 parts); needs
+                             16x16 tiles, fp16x2 = 0 and the one-CTA-per-tile launch;
+                             forward only (gs_render_backward: GS_ERR_UNSUPPORTED) */
+    int32_t reserved[3];
 } gs_config;
 
 /* Fills a config with the defaults above for a kernel kind (plus 16x16

@@ -35,7 +35,8 @@ class GsConfig(C.Structure):
                 ("eps", C.c_float), ("alpha_max", C.c_float), ("t_min", C.c_float),
                 ("aa_normalize", C.c_int32), ("aa_dilation", C.c_float), ("tile_w", C.c_int32),
                 ("tile_h", C.c_int32), ("rect_mode", C.c_int32), ("batch", C.c_int32),
-                ("px_per_thread", C.c_int32), ("fp16x2", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("px_per_thread", C.c_int32), ("fp16x2", C.c_int32), ("tensor_alpha", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class GsError(RuntimeError):

@@ -448,7 +448,7 @@ extern "C" gs_status gs_render_backward(void *stream, const gs_camera *cams, int
     if (cfg->tile_w * cfg->tile_h > 256) return GS_ERR_UNSUPPORTED;
     // the reverse pass recomputes alpha in FP32; an FP16x2 forward could have
     // taken different skip / stop decisions
-    if (cfg->fp16x2) return GS_ERR_UNSUPPORTED;
+    if (cfg->fp16x2 || cfg->tensor_alpha) return GS_ERR_UNSUPPORTED;
     const int64_t N = (int64_t)ncam * P;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(d_grad2d, 0, gs_grad2d_bytes(ncam, P), s) != cudaSuccess) return GS_ERR_CUDA;

@@ -267,6 +267,170 @@ render_persistent_kernel(const __grid_constant__ CamTable cams, const __grid_con
     }
 }
 
+// ---- Tensor-core evaluation of the quadric (the paper's Sec. 5.1 argument) ----
+// For a 16x16 tile the quadric of every (pixel, splat) pair of a batch is one
+// small contraction: Q = Phi(pixel) . W(splat) with the 6 monomials
+// Phi = (x^2, x y, y^2, x, y, 1) of tile-centred pixel coordinates and
+// W = (A, 2B, C, -2(A dx0 + B dy0), -2(B dx0 + C dy0), Q(tile centre)), K padded
+// to 8. Each warp computes its 32 pixels x kTcB splats with mma.sync TF32;
+// the pixel monomials are exact in TF32 (quarter integers below 57) and the
+// splat weights are split into two TF32 parts (hi + lo), so A.B_hi + A.B_lo
+// carries the weights' FP32 precision. The blend then reads Q per pixel from
+// shared memory and composites in order as the FP32 path does (alpha from
+// the same kernel function, same thresholds). One pixel per thread.
+constexpr int kTcB = 32;        // splats per batch
+constexpr int kTcS = kTcB + 4;  // Q row stride (words): conflict-free 16-byte row reads
+constexpr int kTcWS = kTcB + 8; // weight row stride (words): conflict-free fragment loads
+
+__device__ __forceinline__ uint32_t to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_tf32_16x8x8(float &c0, float &c1, float &c2, float &c3, const uint32_t a[4],
+                                                uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(c0), "+f"(c1), "+f"(c2), "+f"(c3)
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// monomial `k` of the tile-centred pixel position (xc, yc)
+__device__ __forceinline__ float monomial(int k, float xc, float yc)
+{
+    return k == 0 ? xc * xc : k == 1 ? xc * yc : k == 2 ? yc * yc : k == 3 ? xc : k == 4 ? yc : k == 5 ? 1.f : 0.f;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256)
+render_tc_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
+                 const __grid_constant__ RenderArgs g)
+{
+    __shared__ __align__(16) float s_q[256 * kTcS];
+    __shared__ uint32_t s_whi[8 * kTcWS], s_wlo[8 * kTcWS];
+    __shared__ float4 s_b[kTcB], s_c[kTcB];
+    const int gtile = blockIdx.x;
+    int c = 0;
+    while (c + 1 < cams.ncam && cams.cam[c + 1].tile_base <= gtile) ++c;
+    const CamDev &cm = cams.cam[c];
+    const int lt = gtile - cm.tile_base;
+    const int tx = lt % cm.tiles_x, ty = lt / cm.tiles_x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lx = tid & 15, ly = tid >> 4;
+    const int px = tx * 16 + lx, py = ty * 16 + ly;
+    const float ox = (float)(tx * 16), oy = (float)(ty * 16);
+    const float ocx = ox + 8.f, ocy = oy + 8.f; // tile centre
+    const uint2 rg = g.ranges[gtile];
+    const uint32_t n = rg.y - rg.x;
+    const float eps = cfg.eps, amax = cfg.alpha_max, tmin = cfg.t_min;
+    bool active = px < cm.W && py < cm.H;
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+    float ek = active ? eps : INFINITY;
+    uint32_t lastc = 0, ne = n;
+    // A fragments (m16n8k8, row-major 16 x 8): warp w, m-tile mt holds tile row
+    // 2w + mt, fragment row r = pixel column r; element e of the fragment is
+    // (row g + 8 (e & 1), column t + 4 (e >> 1)) with g = lane / 4, t = lane % 4
+    const int gq = lane >> 2, tq = lane & 3;
+    uint32_t afr[2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        const float yc = (float)(2 * warp + mt) + 0.5f - 8.f;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float xc = (float)(gq + 8 * (e & 1)) + 0.5f - 8.f;
+            afr[mt][e] = to_tf32(monomial(tq + 4 * (e >> 1), xc, yc)); // exact
+        }
+    }
+    const float *qrow = s_q + tid * kTcS;
+    for (uint32_t base = 0; base < n; base += kTcB) {
+        if (__syncthreads_count(active) == 0) break;
+        const int cnt = (int)min((uint32_t)kTcB, n - base);
+        if (tid < kTcB) {
+            float w[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float4 bb = make_float4(0.f, 0.f, 0.f, 0.f), cc = bb;
+            if (tid < cnt) {
+                uint32_t v = g.vals[rg.x + base + tid];
+                if (v >= g.n_records) v = 0; // only after a timed-out sort wait
+                const float4 r0 = g.rec[3 * (size_t)v + 0], r1 = g.rec[3 * (size_t)v + 1];
+                const float4 r2 = g.rec[3 * (size_t)v + 2];
+                const BlendCoef k = make_coef<KIND>(cfg, r0, r1, r2, ox, oy);
+                bb = k.b;
+                cc = k.c;
+                const float A = r1.x, B = r1.y, C = r1.z;
+                const float dx0 = r0.x - ocx, dy0 = r0.y - ocy;
+                const float gx = fmaf(A, dx0, B * dy0), gy = fmaf(B, dx0, C * dy0);
+                w[0] = A;
+                w[1] = 2.f * B;
+                w[2] = C;
+                w[3] = -2.f * gx;
+                w[4] = -2.f * gy;
+                w[5] = fmaf(dx0, gx, dy0 * gy);
+            }
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const uint32_t hi = to_tf32(w[kk]);
+                s_whi[kk * kTcWS + tid] = hi;
+                s_wlo[kk * kTcWS + tid] = to_tf32(w[kk] - __uint_as_float(hi));
+            }
+            s_b[tid] = bb;
+            s_c[tid] = cc;
+        }
+        __syncthreads();
+        if (__any_sync(0xffffffffu, active)) {
+#pragma unroll
+            for (int nt = 0; nt < kTcB / 8; ++nt) {
+                const int n0 = nt * 8;
+                // B fragment (col-major 8 x 8): (row t, column g) and (row t + 4, column g)
+                const uint32_t bh0 = s_whi[tq * kTcWS + n0 + gq], bh1 = s_whi[(tq + 4) * kTcWS + n0 + gq];
+                const uint32_t bl0 = s_wlo[tq * kTcWS + n0 + gq], bl1 = s_wlo[(tq + 4) * kTcWS + n0 + gq];
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+                    mma_tf32_16x8x8(c0, c1, c2, c3, afr[mt], bl0, bl1); // small part first
+                    mma_tf32_16x8x8(c0, c1, c2, c3, afr[mt], bh0, bh1);
+                    // C fragment: (row g, columns 2t, 2t + 1) and (row g + 8, same columns)
+                    const int p0 = 32 * warp + 16 * mt + gq;
+                    *reinterpret_cast<float2 *>(&s_q[p0 * kTcS + n0 + 2 * tq]) = make_float2(c0, c1);
+                    *reinterpret_cast<float2 *>(&s_q[(p0 + 8) * kTcS + n0 + 2 * tq]) = make_float2(c2, c3);
+                }
+            }
+        }
+        __syncwarp(); // a pixel's Q row is written by its own warp
+        for (int j = 0; j < cnt && active; ++j) {
+            const float4 cj = s_c[j];
+            const float al0 = alpha_of_q<KIND>(cfg, s_b[j], cj.w, qrow[j]);
+            if (!(al0 >= ek)) continue;
+            const float al = fminf(amax, al0);
+            const float Tn = fmaf(-al, T, T);
+            const uint32_t pos = base + j + 1;
+            if (Tn < tmin) {
+                active = false;
+                ek = INFINITY;
+                ne = pos;
+                break;
+            }
+            const float wgt = al * T;
+            C0 = fmaf(cj.x, wgt, C0);
+            C1 = fmaf(cj.y, wgt, C1);
+            C2 = fmaf(cj.z, wgt, C2);
+            T = Tn;
+            lastc = pos;
+        }
+    }
+    if (px < cm.W && py < cm.H) {
+        const int64_t pix = cm.pix_base + (int64_t)py * cm.W + px;
+        g.out[3 * pix + 0] = fmaf(T, g.bg0, C0);
+        g.out[3 * pix + 1] = fmaf(T, g.bg1, C1);
+        g.out[3 * pix + 2] = fmaf(T, g.bg2, C2);
+        if (g.final_T) g.final_T[pix] = T;
+        if (g.last) g.last[pix] = lastc;
+        if (g.n_eval) g.n_eval[pix] = ne;
+    }
+}
+
 template <int KIND, int PPT, bool HALF>
 cudaError_t launch2(int threads, cudaStream_t s, const CamTable &t, const CfgDev &c, const RenderArgs &g,
                     uint32_t *work)
@@ -323,6 +487,9 @@ extern "C" gs_status gs_render(void *stream, const gs_camera *cams, int32_t ncam
     const int ppt = cfg->px_per_thread;
     if (ppt != 1 && ppt != 2 && ppt != 4) return GS_ERR_ARG;
     if (cfg->batch < 1 || cfg->batch > kMaxBatch) return GS_ERR_ARG;
+    if (cfg->tensor_alpha != 0 && cfg->tensor_alpha != 1) return GS_ERR_ARG;
+    if (cfg->tensor_alpha && (cfg->tile_w != 16 || cfg->tile_h != 16 || cfg->fp16x2 || d_work))
+        return GS_ERR_UNSUPPORTED; // tensor-core variant: 16x16 tiles, FP32, one CTA per tile
     const bool half = cfg->fp16x2 != 0;
     if (half && ppt == 1) return GS_ERR_ARG; // packed pairs need 2 or 4 pixels per thread
     if (cfg->tile_w % ppt) return GS_ERR_ARG;
@@ -342,11 +509,21 @@ extern "C" gs_status gs_render(void *stream, const gs_camera *cams, int32_t ncam
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     uint32_t *work = static_cast<uint32_t *>(d_work);
     cudaError_t e;
+    if (cfg->tensor_alpha) {
+        switch (cfg->kind) {
+        case GS_K_EXP: render_tc_kernel<GS_K_EXP><<<t.total_tiles, 256, 0, s>>>(t, c, g); break;
+        case GS_K_POLY1: render_tc_kernel<GS_K_POLY1><<<t.total_tiles, 256, 0, s>>>(t, c, g); break;
+        case GS_K_POLY2: render_tc_kernel<GS_K_POLY2><<<t.total_tiles, 256, 0, s>>>(t, c, g); break;
+        default: render_tc_kernel<GS_K_POLY3><<<t.total_tiles, 256, 0, s>>>(t, c, g); break;
+        }
+        e = cudaPeekAtLastError();
+    } else {
     switch (cfg->kind) {
     case GS_K_EXP: e = launch_render<GS_K_EXP>(ppt, half, threads, s, t, c, g, work); break;
     case GS_K_POLY1: e = launch_render<GS_K_POLY1>(ppt, half, threads, s, t, c, g, work); break;
     case GS_K_POLY2: e = launch_render<GS_K_POLY2>(ppt, half, threads, s, t, c, g, work); break;
     default: e = launch_render<GS_K_POLY3>(ppt, half, threads, s, t, c, g, work); break;
+    }
     }
     count_launch();
     if (e != cudaSuccess) {

@@ -82,7 +82,7 @@ def test_sizes_and_tiles(L):
 def test_host_argument_checks(L):
     """Every entry point rejects invalid arguments before touching the GPU."""
     from paper_2603_18707_b300 import api
-    from paper_2603_18707_b300._lib import GS_ERR_ARG, lib
+    from paper_2603_18707_b300._lib import GS_ERR_ARG, GS_ERR_UNSUPPORTED, lib
     lb = lib()
     cams = api.camera_array([{"viewmat": [[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 3], [0, 0, 0, 1]],
                               "fx": 100, "fy": 100, "cx": 64, "cy": 64, "width": 128,
@@ -122,6 +122,12 @@ def test_host_argument_checks(L):
     bad.batch = 512
     assert lb.gs_render(None, cams, 1, 10, C.byref(bad), ptr, ptr, ptr, bg, ptr, None, None, None,
                         None) == GS_ERR_ARG
+    bad = api.make_config("poly1", "opacity", tensor_alpha=2)
+    assert lb.gs_render(None, cams, 1, 10, C.byref(bad), ptr, ptr, ptr, bg, ptr, None, None, None,
+                        None) == GS_ERR_ARG
+    bad = api.make_config("poly1", "opacity", tensor_alpha=1, tile=(8, 8))
+    assert lb.gs_render(None, cams, 1, 10, C.byref(bad), ptr, ptr, ptr, bg, ptr, None, None, None,
+                        None) == GS_ERR_UNSUPPORTED
     bad = api.make_config("poly1", "opacity", px_per_thread=3)
     assert lb.gs_render(None, cams, 1, 10, C.byref(bad), ptr, ptr, ptr, bg, ptr, None, None, None,
                         None) == GS_ERR_ARG

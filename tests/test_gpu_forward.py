@@ -153,6 +153,50 @@ def test_f2_range_coefficients_match_oracle(gs, orc, small, tile, cull):
     assert n_near < 0.01 * img.shape[0] * img.shape[1]
 
 
+@pytest.mark.parametrize("kind", ["exp", "poly1", "poly2", "poly3"])
+@pytest.mark.parametrize("cull", ["universal", "opacity"])
+def test_tensor_core_quadric_matches_oracle(gs, orc, small, kind, cull):
+    """The tensor-core variant (Q of every pixel-splat pair by mma.sync TF32
+    with split weights) against the untiled FP64 oracle, same tolerance as
+    the FP32 path outside threshold flips."""
+    from paper_2603_18707_b300 import synth
+    cam = synth.camera_small()
+    R = _gpu(gs, small, [cam], kind, cull, tensor_alpha=1)
+    img = R.images()[0].cpu().numpy()
+    oc = orc.camera_from_dict(cam)
+    sc = orc.activate(small)
+    ref, _, _ = orc.render_untiled(sc, oc, _oracle_cfg(orc, kind, cull))
+    *_, margin = orc.render_tiled(sc, oc, orc.make_config(kind, KIND_COEFFS[kind], "universal"),
+                                  with_margin=True)
+    worst, n_near, _ = _compare(img, ref, margin)
+    assert worst < TOL_FP32, (worst, n_near)
+    assert n_near < 0.01 * img.shape[0] * img.shape[1]
+
+
+def test_tensor_core_quadric_full_size_tiles(gs, orc):
+    """3M-splat 1080p scene (splats of every size, far-off centres): sampled
+    tiles of the tensor-core variant against the oracle's tile render."""
+    from paper_2603_18707_b300 import synth
+    raw = synth.scene_clusters(3_000_000, 0, sh_degree=3)
+    cam = synth.orbit_cameras(16, 1920, 1080)[0]
+    R = _gpu(gs, raw, [cam], "poly1", "opacity", keep_keys=False, tensor_alpha=1)
+    img = R.images()[0].cpu().numpy()
+    tx, ty = (1920 + 15) // 16, (1080 + 15) // 16
+    rng = np.random.default_rng(7)
+    tiles = sorted(set(rng.integers(0, tx * ty, 16).tolist()) | {tx * ty - 1})
+    ref, _, _, _, _, margin = orc.render_tiled(orc.activate(raw), orc.camera_from_dict(cam),
+                                               _oracle_cfg(orc, "poly1", "opacity"), tiles=tiles,
+                                               with_margin=True)
+    mask = np.zeros((1080, 1920), bool)
+    for t in tiles:
+        y, x = (t // tx) * 16, (t % tx) * 16
+        mask[y:y + 16, x:x + 16] = True
+    err = np.abs(img.astype(np.float64) - ref).max(-1)
+    near = margin < NEAR_MARGIN
+    assert err[mask & ~near].max() < TOL_FP32
+    assert (mask & near).sum() < 0.02 * mask.sum()
+
+
 def test_poly1_vs_exp_psnr_reported(gs, small):
     """Sec. 4.1 trend on the config-1 scene: f3 is closer to exp than f1."""
     from paper_2603_18707_b300 import synth
