@@ -87,6 +87,8 @@ def parse():
     p.add_argument("--no-fp16", action="store_true", help="skip the FP16x2 precision leg")
     p.add_argument("--no-f2range", action="store_true", help="skip the range-extended f2 leg")
     p.add_argument("--no-tensor", action="store_true", help="skip the tensor-core quadric leg")
+    p.add_argument("--groups", type=int, default=2,
+                   help="camera sets issued on streams of their own (1: one stream)")
     p.add_argument("--ppt", type=int, default=None, help="pixels per blend thread (1, 2, 4)")
     p.add_argument("--tile", type=str, default=None, help="tile shape WxH, e.g. 16x16")
     p.add_argument("--rect", choices=["aabb", "circle", "ellipse"], default=None,
@@ -102,6 +104,7 @@ def workload(a):
             "splats": a.splats, "cameras": a.cams, "resolution": f"{a.width}x{a.height}",
             "sh_degree": 3, "tile": "16x16", "kernel": "poly1", "cull": "opacity",
             "baseline_kernel": "exp", "baseline_cull": "opacity",
+            "camera_sets_on_streams": getattr(a, "groups", 1),
             "l2": "inputs larger than L2 (scene 0.7 GB, records 3 GB per step)"}
 
 
@@ -296,8 +299,13 @@ def run_ours(a, world, rank, local):
                               "records_drawn_overlaps": list(r.n_records()),
                               "launches_per_step": 14}), flush=True)
         return
-    R = {"poly1": render.Rasterizer(cams, api.make_config("poly1", "opacity", **over), P),
-         "exp": render.Rasterizer(cams, api.make_config("exp", "opacity", **over), P)}
+    def make(kind):
+        cfg = api.make_config(kind, "opacity", **over)
+        if a.groups > 1:
+            return render.StreamedRasterizer(cams, cfg, P, groups=a.groups)
+        return render.Rasterizer(cams, cfg, P)
+
+    R = {"poly1": make("poly1"), "exp": make("exp")}
     evals, psnr = {}, []
     for k, r in R.items():
         r.forward(sc, n_eval=True)  # sizes the overlap buffers, counts evaluations

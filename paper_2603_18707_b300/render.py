@@ -30,7 +30,9 @@ class Rasterizer:
     """Renders P splats into a fixed list of cameras (at most 64)."""
 
     def __init__(self, cams, cfg, P: int, capacity: int | None = None, device="cuda",
-                 keep_keys: bool = False, persistent: bool = False):
+                 keep_keys: bool = False, persistent: bool = False, outputs: dict | None = None):
+        """outputs: optional views (out [npix, 3], final_T, last, n_eval [npix])
+        to render into instead of buffers of its own."""
         self.cams = api.camera_array(cams)
         self.ncam = len(self.cams)
         self.cfg = cfg
@@ -44,10 +46,14 @@ class Rasterizer:
         self.splat2d = torch.empty(api.gs_splat2d_bytes(self.ncam, self.P), **u8)
         self.ranges = torch.zeros(2 * self.total_tiles, **i32)
         self.count = torch.zeros(3, **i32)
-        self.out = torch.empty(self.npix, 3, dtype=torch.float32, device=self.device)
-        self.final_T = torch.empty(self.npix, dtype=torch.float32, device=self.device)
-        self.last = torch.empty(self.npix, **i32)
-        self.n_eval = torch.empty(self.npix, **i32)
+        if outputs is not None:
+            self.out, self.final_T = outputs["out"], outputs["final_T"]
+            self.last, self.n_eval = outputs["last"], outputs["n_eval"]
+        else:
+            self.out = torch.empty(self.npix, 3, dtype=torch.float32, device=self.device)
+            self.final_T = torch.empty(self.npix, dtype=torch.float32, device=self.device)
+            self.last = torch.empty(self.npix, **i32)
+            self.n_eval = torch.empty(self.npix, **i32)
         self.keep_keys = keep_keys
         self.work = (torch.zeros(api.gs_render_work_bytes(), **u8) if persistent else None)
         self.shrink = capacity is None  # an explicit capacity is kept as given
@@ -139,3 +145,86 @@ class Rasterizer:
     def n_records(self) -> tuple[int, int]:
         c = self.count.cpu().tolist()
         return c[0] & 0xFFFFFFFF, c[1] & 0xFFFFFFFF
+
+
+class StreamedRasterizer:
+    """The cameras split into `groups` consecutive sets, each with a
+    Rasterizer of its own rendering into its slice of shared output buffers,
+    and each set's pass (preprocess, bin/sort, blend) issued on a stream of
+    its own: one set's latency-bound sort overlaps another's ALU-bound blend.
+    Same interface as Rasterizer; the work per pass is the same."""
+
+    def __init__(self, cams, cfg, P: int, groups: int = 2, device="cuda", keep_keys: bool = False):
+        cams = list(cams)
+        groups = max(1, min(int(groups), len(cams)))
+        bounds = [round(k * len(cams) / groups) for k in range(groups + 1)]
+        sets = [cams[bounds[k]:bounds[k + 1]] for k in range(groups)]
+        self.cams = api.camera_array(cams)
+        self.ncam = len(cams)
+        self.cfg = cfg
+        self.P = int(P)
+        self.device = torch.device(device)
+        self.sizes = [(c.height, c.width) for c in self.cams]
+        self.npix = sum(h * w for h, w in self.sizes)
+        i32 = dict(dtype=torch.int32, device=self.device)
+        self.out = torch.empty(self.npix, 3, dtype=torch.float32, device=self.device)
+        self.final_T = torch.empty(self.npix, dtype=torch.float32, device=self.device)
+        self.last = torch.empty(self.npix, **i32)
+        self.n_eval = torch.empty(self.npix, **i32)
+        self.parts, o = [], 0
+        for cs in sets:
+            n = sum(c["height"] * c["width"] for c in cs)
+            views = {"out": self.out[o:o + n], "final_T": self.final_T[o:o + n],
+                     "last": self.last[o:o + n], "n_eval": self.n_eval[o:o + n]}
+            self.parts.append(Rasterizer(cs, cfg, P, device=device, keep_keys=keep_keys, outputs=views))
+            o += n
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in self.parts]
+
+    def preprocess(self, sc: dict):
+        for r in self.parts:
+            r.preprocess(sc)
+
+    def bin_sort(self):
+        for r in self.parts:
+            r.bin_sort()
+
+    def blend(self, bg=(0.0, 0.0, 0.0), n_eval: bool = True):
+        for r in self.parts:
+            r.blend(bg, n_eval)
+
+    def forward(self, sc: dict, bg=(0.0, 0.0, 0.0), n_eval: bool = True):
+        for r in self.parts:
+            r.forward(sc, bg, n_eval)
+        return self.out
+
+    def run_async(self, sc: dict, bg=(0.0, 0.0, 0.0), n_eval: bool = False):
+        cur = torch.cuda.current_stream(self.device)
+        for r, st in zip(self.parts, self.streams):
+            st.wait_stream(cur)
+            with torch.cuda.stream(st):
+                r.run_async(sc, bg, n_eval)
+        for st in self.streams:
+            cur.wait_stream(st)
+        return self.out
+
+    def capture(self, sc: dict, bg=(0.0, 0.0, 0.0), n_eval: bool = False):
+        side = torch.cuda.Stream(device=self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(side):
+            self.run_async(sc, bg, n_eval)
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self.run_async(sc, bg, n_eval)
+        return graph
+
+    def images(self):
+        return Rasterizer.images(self)
+
+    def per_camera(self, t):
+        return Rasterizer.per_camera(self, t)
+
+    def n_records(self) -> tuple[int, int]:
+        recs = [r.n_records() for r in self.parts]
+        return sum(a for a, _ in recs), sum(b for _, b in recs)
