@@ -121,22 +121,18 @@ struct TilePlan {
 
 TilePlan tile_plan(int64_t total_tiles)
 {
+    // as few passes as 9-bit digits allow, and within them as many 8-bit
+    // digits as possible (an 8-bit pass is ~25% cheaper per key); the widest
+    // digit first (the look-back state is sized by it). Up to 27 bits
+    // (< 2^30 tiles is checked by the caller).
     int b = 1;
     while (((int64_t)1 << b) < total_tiles) ++b;
     TilePlan p{};
-    if (b <= 8) {
-        p.passes = 1; p.bits[0] = 8;
-    } else if (b <= 16) {
-        p.passes = 2; p.bits[0] = p.bits[1] = 8;
-    } else if (b <= 18) {
-        p.passes = 2; p.bits[0] = p.bits[1] = 9;
-    } else if (b <= 24) {
-        p.passes = 3; p.bits[0] = p.bits[1] = p.bits[2] = 8;
-    } else {
-        p.passes = 3; p.bits[0] = p.bits[1] = p.bits[2] = 9; // up to 2^27 tiles (< 2^30 checked)
-    }
+    p.passes = std::max(1, (b + 8) / 9);
+    const int nine = std::max(0, b - 8 * p.passes);
     int s = 0;
     for (int i = 0; i < p.passes; ++i) {
+        p.bits[i] = i < nine ? 9 : 8;
         p.shift[i] = s;
         s += p.bits[i];
     }
