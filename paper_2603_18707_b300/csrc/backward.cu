@@ -80,7 +80,9 @@ blend_backward_kernel(const __grid_constant__ CamTable cams, const __grid_consta
     __syncthreads();
     if (L) atomicMax(&s_maxL, L);
     __syncthreads();
-    const int maxL = (int)min(s_maxL, rg.y - rg.x); // a pixel's last lies within its tile list
+    // a pixel's last lies within its tile list (an inverted range, only
+    // possible after a timed-out sort wait, counts as empty)
+    const int maxL = (int)min(s_maxL, rg.y > rg.x ? rg.y - rg.x : 0u);
     const int B = blockDim.x;
     const float eps = cfg.eps, amax = cfg.alpha_max;
     for (int end = maxL; end > 0; end -= B) {

@@ -30,6 +30,10 @@ namespace gs {
 namespace {
 
 constexpr int kMaxBatch = 256;
+#ifndef GS_BLEND_UNROLL
+#define GS_BLEND_UNROLL 1 // unroll of the per-entry loop (ILP across entries)
+#endif
+constexpr int kBlendUnroll = GS_BLEND_UNROLL;
 #ifndef GS_RENDER_MIN_BLOCKS
 #define GS_RENDER_MIN_BLOCKS 4 // 256-thread CTAs per SM the register budget must allow (64 registers: measured fastest)
 #endif
@@ -98,7 +102,9 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
     const int px0 = tx * cfg.tile_w + lx, py = ty * cfg.tile_h + ly;
     const float y = ly + 0.5f;
     const uint2 rg = g.ranges[gtile];
-    const uint32_t n = rg.y - rg.x;
+    // an empty or inverted range (only possible after a timed-out sort wait)
+    // reads nothing: every range gs_bin_sort writes lies within its output
+    const uint32_t n = rg.y > rg.x ? rg.y - rg.x : 0u;
     const int nthreads = blockDim.x;
     const int B = cfg.batch;
 
@@ -141,6 +147,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)B, n - base);
+#pragma unroll kBlendUnroll
         for (int j = 0; j < cnt && active; ++j) {
             const float4 a = s_a[j];
             const float4 b = s_b[j];
@@ -324,7 +331,9 @@ render_tc_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ 
     const float ox = (float)(tx * 16), oy = (float)(ty * 16);
     const float ocx = ox + 8.f, ocy = oy + 8.f; // tile centre
     const uint2 rg = g.ranges[gtile];
-    const uint32_t n = rg.y - rg.x;
+    // an empty or inverted range (only possible after a timed-out sort wait)
+    // reads nothing: every range gs_bin_sort writes lies within its output
+    const uint32_t n = rg.y > rg.x ? rg.y - rg.x : 0u;
     const float eps = cfg.eps, amax = cfg.alpha_max, tmin = cfg.t_min;
     bool active = px < cm.W && py < cm.H;
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
