@@ -31,7 +31,7 @@ namespace {
 
 constexpr int kMaxBatch = 256;
 #ifndef GS_BLEND_UNROLL
-#define GS_BLEND_UNROLL 1 // unroll of the per-entry loop (ILP across entries)
+#define GS_BLEND_UNROLL 4 // unroll of the per-entry loop (ILP across entries; 4 measured fastest)
 #endif
 constexpr int kBlendUnroll = GS_BLEND_UNROLL;
 #ifndef GS_RENDER_MIN_BLOCKS
