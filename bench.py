@@ -99,7 +99,7 @@ def parse():
 
 
 def workload(a):
-    return {"workload": f"{a.splats // 1_000_000}M-splat cluster scene, SH degree 3, "
+    return {"workload": f"{a.splats / 1e6:g}M-splat cluster scene, SH degree 3, "
                         f"{a.cams} orbit cameras at {a.width}x{a.height}",
             "splats": a.splats, "cameras": a.cams, "resolution": f"{a.width}x{a.height}",
             "sh_degree": 3, "tile": "16x16", "kernel": "poly1", "cull": "opacity",
