@@ -228,3 +228,64 @@ class StreamedRasterizer:
     def n_records(self) -> tuple[int, int]:
         recs = [r.n_records() for r in self.parts]
         return sum(a for a, _ in recs), sum(b for _, b in recs)
+
+
+class HostPipeline:
+    """Frames from pinned host inputs to pinned host images: step k's
+    upload and step k-1's download run on copy streams of their own while
+    the rasterizer renders, with two device copies of the inputs and of the
+    image so that no step waits for a copy it does not need. Every step
+    uploads its whole input and downloads its whole image."""
+
+    KEYS = ("means", "scales", "quats", "opacities", "sh")
+
+    def __init__(self, raster, upload_streams: int = 1):
+        self.R = raster
+        dev = raster.out.device
+        # uploads may be split by rows over several copy streams (measured:
+        # one stream already runs at the host link's rate)
+        self.up = [torch.cuda.Stream(device=dev) for _ in range(max(1, int(upload_streams)))]
+        self.h2d = self.up[0]
+        self.d2h = torch.cuda.Stream(device=dev)
+        self.dev_in = [None, None]
+        self.dev_out = [torch.empty_like(raster.out) for _ in range(2)]
+        self.ev_in_free = [torch.cuda.Event(), torch.cuda.Event()]
+        self.ev_uploaded = [torch.cuda.Event(), torch.cuda.Event()]
+        self.ev_rendered = [torch.cuda.Event(), torch.cuda.Event()]
+        self.ev_out_free = [torch.cuda.Event(), torch.cuda.Event()]
+        self.k = 0
+
+    def step(self, host_in: dict, host_out: torch.Tensor):
+        """Enqueues one frame: host_in (pinned tensors of the activated scene,
+        plus sh_degree) -> host_out (pinned, the shape of raster.out)."""
+        b = self.k & 1
+        self.k += 1
+        if self.dev_in[b] is None:
+            self.dev_in[b] = {k: torch.empty_like(host_in[k], device=self.R.out.device) for k in self.KEYS}
+            self.dev_in[b]["sh_degree"] = int(host_in["sh_degree"])
+        cur = torch.cuda.current_stream(self.R.out.device)
+        m = len(self.up)
+        for i, st in enumerate(self.up):
+            st.wait_event(self.ev_in_free[b])  # the render that read these inputs is done
+            with torch.cuda.stream(st):
+                for k in self.KEYS:
+                    n = host_in[k].shape[0]
+                    lo, hi = n * i // m, n * (i + 1) // m
+                    self.dev_in[b][k][lo:hi].copy_(host_in[k][lo:hi], non_blocking=True)
+        for st in self.up[1:]:
+            self.h2d.wait_stream(st)
+        self.ev_uploaded[b].record(self.h2d)
+        cur.wait_event(self.ev_uploaded[b])
+        cur.wait_event(self.ev_out_free[b])  # the download of this image buffer is done
+        self.R.run_async(self.dev_in[b])
+        self.dev_out[b].copy_(self.R.out, non_blocking=True)
+        self.ev_in_free[b].record(cur)
+        self.ev_rendered[b].record(cur)
+        self.d2h.wait_event(self.ev_rendered[b])
+        with torch.cuda.stream(self.d2h):
+            host_out.copy_(self.dev_out[b], non_blocking=True)
+            self.ev_out_free[b].record(self.d2h)
+
+    def finish(self):
+        """Makes the current stream wait for every enqueued download."""
+        torch.cuda.current_stream(self.R.out.device).wait_stream(self.d2h)

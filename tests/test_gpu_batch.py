@@ -143,3 +143,29 @@ def test_streamed_camera_groups_equal_single():
         g.replay()
         torch.cuda.synchronize()
         assert torch.equal(st.out, one.out)
+
+
+def test_host_pipeline_frames_match_device_renders():
+    """render.HostPipeline (overlapped upload / render / download): each
+    step's host image equals the device render of that step's own input,
+    with two different scenes alternating."""
+    import torch
+    from paper_2603_18707_b300 import api, render, synth
+    cams = synth.mixed_cameras(3)
+    scenes = [render.activate(synth.scene_clusters(100_000, s, sh_degree=2)) for s in (1, 2)]
+    R = render.StreamedRasterizer(cams, api.make_config("poly1", "opacity"), 100_000, groups=2)
+    want = []
+    for sc in scenes:
+        R.forward(sc)
+        want.append(R.out.clone())
+    hosts = [{k: sc[k].cpu().pin_memory() for k in render.HostPipeline.KEYS} for sc in scenes]
+    for h in hosts:
+        h["sh_degree"] = 2
+    outs = [torch.empty_like(R.out, device="cpu").pin_memory() for _ in range(5)]
+    pipe = render.HostPipeline(R)
+    for k in range(5):
+        pipe.step(hosts[k % 2], outs[k])
+    pipe.finish()
+    torch.cuda.synchronize()
+    for k in range(5):
+        assert torch.equal(outs[k], want[k % 2].cpu()), k
