@@ -30,10 +30,16 @@ namespace gs {
 namespace {
 
 constexpr int kMaxBatch = 256;
+// Unroll of the per-entry loop (ILP across entries): measured fastest at 4
+// for the polynomial kernels and 8 for exp (0: per kind as measured).
 #ifndef GS_BLEND_UNROLL
-#define GS_BLEND_UNROLL 4 // unroll of the per-entry loop (ILP across entries; 4 measured fastest)
+#define GS_BLEND_UNROLL 0
 #endif
-constexpr int kBlendUnroll = GS_BLEND_UNROLL;
+template <int KIND>
+constexpr int blend_unroll()
+{
+    return GS_BLEND_UNROLL ? GS_BLEND_UNROLL : (KIND == GS_K_EXP ? 8 : 4);
+}
 #ifndef GS_RENDER_MIN_BLOCKS
 #define GS_RENDER_MIN_BLOCKS 4 // 256-thread CTAs per SM the register budget must allow (64 registers: measured fastest)
 #endif
@@ -147,7 +153,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)B, n - base);
-#pragma unroll kBlendUnroll
+#pragma unroll blend_unroll<KIND>()
         for (int j = 0; j < cnt && active; ++j) {
             const float4 a = s_a[j];
             const float4 b = s_b[j];
