@@ -63,6 +63,26 @@ def test_mixed_batch_equals_single_cameras(gs, scene):
         assert torch.equal(one.images()[0], im)
 
 
+def test_sixty_four_cameras_the_batch_limit(gs, scene):
+    """The largest camera batch (GS_MAX_CAMERAS = 64, ragged 200x120 frames):
+    every image bit-identical to the same camera rendered alone; 65 cameras
+    are rejected."""
+    api, render, synth = gs
+    raw, sc = scene
+    from paper_2603_18707_b300 import _lib
+    cams = synth.orbit_cameras(64, 200, 120)
+    cfg = api.make_config("poly1", "opacity")
+    R = render.Rasterizer(cams, cfg, 200_000)
+    R.forward(sc)
+    imgs = R.images()
+    for k in (0, 17, 40, 63):
+        one = render.Rasterizer([cams[k]], cfg, 200_000)
+        one.forward(sc)
+        assert torch.equal(one.images()[0], imgs[k]), k
+    with pytest.raises((_lib.GsError, ValueError)):
+        render.Rasterizer(synth.orbit_cameras(65, 200, 120), cfg, 200_000).forward(sc)
+
+
 def test_graph_replay_matches_eager(gs, scene):
     api, render, synth = gs
     raw, sc = scene
