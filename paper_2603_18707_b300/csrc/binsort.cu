@@ -51,7 +51,7 @@ constexpr int kSpinLimit = 1 << 20;
 #define GS_LOOK_WINDOW 1
 #endif
 #ifndef GS_EMIT_MIN_BLOCKS
-#define GS_EMIT_MIN_BLOCKS 6 // 0: no register cap from the occupancy target; 6 measured fastest
+#define GS_EMIT_MIN_BLOCKS 4 // 0: no register cap from the occupancy target; 4 measured fastest
 #endif
 #if GS_EMIT_MIN_BLOCKS
 #define GS_EMIT_BOUNDS __launch_bounds__(256, GS_EMIT_MIN_BLOCKS)
@@ -59,13 +59,16 @@ constexpr int kSpinLimit = 1 << 20;
 #define GS_EMIT_BOUNDS __launch_bounds__(256)
 #endif
 #ifndef GS_EMIT_ITEMS
-#define GS_EMIT_ITEMS 4
+#define GS_EMIT_ITEMS 8
 #endif
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = GS_SORT_ITEMS;
 constexpr int kSortTile = kSortThreads * kSortItems; // keys per partition
-constexpr int kCompactVec = 8;                       // uint4 loads per lane
-constexpr int kCompactTile = 256 * 4 * kCompactVec;  // 8192 records per partition
+#ifndef GS_COMPACT_VEC
+#define GS_COMPACT_VEC 8
+#endif
+constexpr int kCompactVec = GS_COMPACT_VEC;          // uint4 loads per lane
+constexpr int kCompactTile = 256 * 4 * kCompactVec;  // records per partition
 constexpr int kEmitItems = GS_EMIT_ITEMS;
 constexpr int kEmitTile = 256 * kEmitItems;          // records per partition
 constexpr int kHistSlot = 512;                       // histogram entries per pass
@@ -307,7 +310,8 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp
 
 // 1. compaction of drawn records, index order preserved, plus the histograms
 // of the four depth digits. Lane l of warp w holds records
-// base + 1024 w + 4 (32 j + l) + e, e < 4, j < kCompactVec (uint4 loads).
+// base + (kCompactTile / 8) w + 4 (32 j + l) + e, e < 4, j < kCompactVec
+// (uint4 loads).
 __global__ void __launch_bounds__(256)
 compact_kernel(const uint32_t *__restrict__ tiles, const uint32_t *__restrict__ dkey, uint32_t N,
                uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, WsHeader *hdr,
