@@ -40,6 +40,9 @@ constexpr int blend_unroll()
 {
     return GS_BLEND_UNROLL ? GS_BLEND_UNROLL : (KIND == GS_K_EXP ? 8 : 4);
 }
+#ifndef GS_SKIP_MID
+#define GS_SKIP_MID 1 // per-thread skip bound from the run's centre (1) or its two ends (0)
+#endif
 #ifndef GS_RENDER_MIN_BLOCKS
 #define GS_RENDER_MIN_BLOCKS 4 // 256-thread CTAs per SM the register budget must allow (64 registers: measured fastest)
 #endif
@@ -107,6 +110,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
     const float ox = (float)(tx * cfg.tile_w), oy = (float)(ty * cfg.tile_h);
     const int px0 = tx * cfg.tile_w + lx, py = ty * cfg.tile_h + ly;
     const float y = ly + 0.5f;
+    const float xmid = lx + 0.5f * PPT; // centre of the thread's run of pixel centres
     const uint2 rg = g.ranges[gtile];
     // an empty or inverted range (only possible after a timed-out sort wait)
     // reads nothing: every range gs_bin_sort writes lies within its output
@@ -162,13 +166,19 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
             const float v2 = vv * vv;
             const float p3 = (KIND == GS_K_POLY3) ? s_c[j].w : 0.f; // the cubic's top coefficient
             if (PPT > 1 && cfg.monotone) {
-                // smallest Q over this thread's run of pixels: v^2 if u changes
-                // sign along the run, else at the end with the smaller |u|.
-                // With k non-increasing, alpha there bounds every pixel's; the
-                // skip threshold sits below eps so that rounding can never
-                // skip an entry that a pixel would take.
+                // smallest Q over this thread's run of pixels: u is affine
+                // along the run with slope ux = a.x > 0, so its smallest |u|
+                // is max(0, |u(run centre)| - half-width * ux) (0 when u
+                // changes sign). With k non-increasing, alpha there bounds
+                // every pixel's; the skip threshold sits below eps so that
+                // rounding can never skip an entry that a pixel would take.
+#if GS_SKIP_MID
+                const float umid = fmaf(a.x, xmid, ub);
+                const float um = fmaxf(fmaf(-0.5f * (PPT - 1), a.x, fabsf(umid)), 0.f);
+#else
                 const float ua = fmaf(a.x, xs[0], ub), uz = fmaf(a.x, xs[PPT - 1], ub);
                 const float um = ((ua > 0.f) != (uz > 0.f)) ? 0.f : fminf(fabsf(ua), fabsf(uz));
+#endif
                 if (alpha_of_q<KIND>(cfg, b, p3, fmaf(um, um, v2)) < eps_skip) continue;
             }
             float al[PPT];
