@@ -90,21 +90,22 @@ preprocess_kernel(const __grid_constant__ CamTable cams, const __grid_constant__
                   const float *__restrict__ sh, Splat2DPtrs out)
 {
     constexpr int K = (D + 1) * (D + 1), F = 3 * K;
-    // the CTA's SH coefficients, transposed ([coefficient][splat]) so that a
-    // warp reading one coefficient of its 32 splats hits 32 banks; staged once
-    // and read for every camera (kept out of registers: higher occupancy)
-    __shared__ float s_sh[F * 128];
+    // The CTA's SH coefficients, staged once and read for every camera (kept
+    // out of registers: higher occupancy). When a splat's F floats are whole
+    // 16-byte chunks (degrees 1 and 3) each splat keeps a row of its own,
+    // read with 16-byte loads; the row stride (in chunks) is odd, so that 8
+    // lanes reading the same chunk of their rows cover all 32 banks.
+    // Otherwise the layout is transposed ([coefficient][splat]).
+    constexpr bool kRows = F % 4 == 0;
+    constexpr int FS = kRows ? ((F / 4) % 2 ? F : F + 4) : F; // floats per staged row
+    __shared__ __align__(16) float s_sh[kRows ? FS * 128 : F * 128];
     const int i0 = blockIdx.x * 128, i = i0 + (int)threadIdx.x;
     const int nb = min(128, P - i0);
     const float *src = sh + (size_t)i0 * F;
-    if (F % 4 == 0) {
+    if (kRows) {
         for (int e = threadIdx.x; e < nb * F / 4; e += 128) {
-            const float4 v = reinterpret_cast<const float4 *>(src)[e];
             const int sp = (4 * e) / F, j = 4 * e - sp * F; // the four floats share a splat
-            s_sh[(j + 0) * 128 + sp] = v.x;
-            s_sh[(j + 1) * 128 + sp] = v.y;
-            s_sh[(j + 2) * 128 + sp] = v.z;
-            s_sh[(j + 3) * 128 + sp] = v.w;
+            *reinterpret_cast<float4 *>(&s_sh[sp * FS + j]) = reinterpret_cast<const float4 *>(src)[e];
         }
     } else {
         for (int e = threadIdx.x; e < nb * F; e += 128) {
@@ -114,7 +115,6 @@ preprocess_kernel(const __grid_constant__ CamTable cams, const __grid_constant__
     }
     __syncthreads();
     if (i >= P) return;
-    const float *coef = s_sh + threadIdx.x; // coefficient j at coef[128 j]
 
     const float mx = means[3 * i + 0], my = means[3 * i + 1], mz = means[3 * i + 2];
     const float sx = scales[3 * i + 0], sy = scales[3 * i + 1], sz = scales[3 * i + 2];
@@ -222,14 +222,28 @@ preprocess_kernel(const __grid_constant__ CamTable cams, const __grid_constant__
                         dx *= il; dy *= il; dz *= il;
                         float Y[K];
                         sh_basis<D>(dx, dy, dz, Y);
-                        float col[3];
+                        float col[3] = {0.f, 0.f, 0.f};
+                        if constexpr (kRows) {
+                            // coefficient m = 3 k + ch of this splat's row, 4 per load
+                            const float4 *row = reinterpret_cast<const float4 *>(s_sh + threadIdx.x * FS);
 #pragma unroll
-                        for (int ch = 0; ch < 3; ++ch) {
-                            float acc = 0.f;
+                            for (int q = 0; q < F / 4; ++q) {
+                                const float4 c4 = row[q];
+                                const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
-                            for (int k = 0; k < K; ++k) acc = fmaf(Y[k], coef[128 * (3 * k + ch)], acc);
-                            col[ch] = fmaxf(acc + 0.5f, 0.f);
+                                for (int e = 0; e < 4; ++e)
+                                    col[(4 * q + e) % 3] = fmaf(Y[(4 * q + e) / 3], cv[e], col[(4 * q + e) % 3]);
+                            }
+                        } else {
+                            const float *coef = s_sh + threadIdx.x; // coefficient m at coef[128 m]
+#pragma unroll
+                            for (int ch = 0; ch < 3; ++ch) {
+#pragma unroll
+                                for (int k = 0; k < K; ++k) col[ch] = fmaf(Y[k], coef[128 * (3 * k + ch)], col[ch]);
+                            }
                         }
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) col[ch] = fmaxf(col[ch] + 0.5f, 0.f);
                         r2 = make_float4(col[0], col[1], col[2], rho);
                     }
                 }
