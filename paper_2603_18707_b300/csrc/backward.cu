@@ -34,6 +34,45 @@ __device__ __forceinline__ float wsum(float v)
     return v;
 }
 
+// Warp sums of 8 values at once: at the exchanges across 16, 8 and 4 lanes
+// each lane keeps half of its remaining values and sends the other half to
+// its partner (4 + 2 + 1 shuffles), then two plain steps (2 shuffles) finish
+// the single value left. Returns the sum of value (lane >> 2) & 7 (bit 4 of
+// the lane picks the upper half first), valid in every lane; lanes with
+// (lane & 3) == 0 hold the 8 different sums.
+__device__ __forceinline__ float wsum8(const float (&v)[8], int lane)
+{
+    float a[4], b[2];
+    const bool h4 = lane & 16, h2 = lane & 8, h1 = lane & 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = h4 ? v[i] : v[i + 4];
+        const float keep = h4 ? v[i + 4] : v[i];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = h2 ? a[i] : a[i + 2];
+        const float keep = h2 ? a[i + 2] : a[i];
+        b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float c;
+    {
+        const float send = h1 ? b[0] : b[1];
+        const float keep = h1 ? b[1] : b[0];
+        c = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    return c;
+}
+
+// value index whose total wsum8 leaves in this lane
+__device__ __forceinline__ int wsum8_index(int lane)
+{
+    return ((lane & 16) ? 4 : 0) + ((lane & 8) ? 2 : 0) + ((lane & 4) ? 1 : 0);
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(256)
 blend_backward_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
@@ -140,14 +179,12 @@ blend_backward_kernel(const __grid_constant__ CamTable cams, const __grid_consta
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-                for (int t = 0; t < 9; ++t) v[t] = wsum(v[t]);
-                if (lane == 0) {
-                    float *dst = grad2d + (size_t)s_id[jj] * kG2;
-#pragma unroll
-                    for (int t = 0; t < 9; ++t)
-                        if (v[t] != 0.f) atomicAdd(dst + t, v[t]);
-                }
+                const float v8[8] = {v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7]};
+                const float s8 = wsum8(v8, lane);
+                const float s9 = wsum(v[8]);
+                float *dst = grad2d + (size_t)s_id[jj] * kG2;
+                if ((lane & 3) == 0 && s8 != 0.f) atomicAdd(dst + wsum8_index(lane), s8);
+                if (lane == 1 && s9 != 0.f) atomicAdd(dst + 8, s9);
             }
         }
         __syncthreads();
