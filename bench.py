@@ -45,6 +45,38 @@ SMS, FP32_LANES = 148, 128
 BLEND_TRAFFIC = 1440092416 + 643661568
 
 
+def hbm_peak_gbs() -> tuple[float, str]:
+    """The measured HBM copy bandwidth of this GPU model (read + write bytes
+    of a device-to-device copy), else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured copy bandwidth (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback 6.4 TB/s"
+
+
+def binsort_bytes(r) -> dict:
+    """Algorithmic DRAM bytes of one gs_bin_sort call per camera set, from
+    its record and overlap counts: compaction reads the tile count of every
+    record (4 B) and the depth key of every drawn one (4 B) and writes
+    (key, id) (8 B); four 8-bit depth passes read and write 16 B per drawn
+    record each; emission reads the id (4 B) and the tile rectangle and
+    count (12 B) per drawn record and writes (tile, id) (8 B) per overlap;
+    each tile pass reads and writes 16 B per overlap; the ranges kernel
+    reads 4 B per overlap and writes 8 B per tile. For comparison, the
+    3DGS design (one LSD sort of 64-bit (tile | depth) keys with 32-bit
+    ids) moves 8 B (key write) + 24 B per 8-bit pass per overlap."""
+    ours = ref = 0
+    for p in getattr(r, "parts", [r]):
+        drawn, over = p.n_records()
+        bits = max(1, (p.total_tiles - 1).bit_length())
+        tile_passes = max(1, (bits + 8) // 9)
+        ours += (4 * p.ncam * p.P + (12 + 4 * 16 + 16) * drawn
+                 + (8 + 16 * tile_passes + 4) * over + 8 * p.total_tiles)
+        ref += (12 + 24 * math.ceil((bits + 32) / 8)) * over
+    return {"ours": ours, "3dgs_design": ref}
+
+
 def _default_workload(a) -> bool:
     """The configuration BLEND_TRAFFIC was captured on."""
     return ((a.splats, a.cams, a.width, a.height) == (3_000_000, 16, 1920, 1080)
@@ -396,6 +428,16 @@ def run_ours(a, world, rank, local):
                "mode": "render.HostPipeline: each step uploads its inputs and downloads its images; "
                        "step k's upload and step k-1's download overlap step k's render"}
 
+    # bin/sort against HBM: algorithmic bytes per pass over the stage's time
+    hbm, hbm_src = hbm_peak_gbs()
+    sb = binsort_bytes(R["poly1"])
+    sort_s = stages["poly1"]["bin_sort_ms"] / 1e3
+    sort_bin = {"bytes_per_step": sb["ours"], "gbs": sb["ours"] / sort_s / 1e9,
+                "frac": sb["ours"] / sort_s / 1e9 / hbm, "peak_gbs": hbm, "peak_source": hbm_src,
+                "bytes_3dgs_design": sb["3dgs_design"],
+                "gbs_3dgs_design_equivalent": sb["3dgs_design"] / sort_s / 1e9,
+                "note": "bound by look-back and ranking latency, not bandwidth (ncu: 16 % DRAM)"}
+
     # roofline of the dominant kernel: the blend, bound by the FP32 pipes
     st = stages["poly1"]
     dom = max(st, key=st.get)
@@ -447,7 +489,7 @@ def run_ours(a, world, rank, local):
             "speedup_poly1_vs_exp": res["exp"] / ms,
             "psnr_poly1_vs_exp_db": {"mean": float(np.mean(psnr)), "min": float(np.min(psnr))},
             "evals_per_step": evals, "overlaps_per_step": overlaps, "stages_ms": stages,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "roofline": roofline, "sort_bin_hbm": sort_bin, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches}
     line.update(extra)
     print(json.dumps(line), flush=True)
@@ -484,21 +526,30 @@ def bench_differentiable(a):
          for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
     R = render.Rasterizer([cam], cfg, P)
 
-    def step():
+    def step(deferred):
         for v in t.values():
             v.grad = None
-        img = autograd.render(t["means"], t["log_scales"], t["quats"], t["opacity_logits"], t["sh"], 3, R)
+        img = autograd.render(t["means"], t["log_scales"], t["quats"], t["opacity_logits"], t["sh"], 3, R,
+                              deferred=deferred)
         (img - target).abs().mean().backward()
 
+    n = max(5, a.steps // 6)
     for _ in range(3):
-        step()
-    ms = _events_ms(step, max(5, a.steps // 6))
+        step(False)
+    ms_sync = _events_ms(lambda: step(False), n)
+    for _ in range(3):
+        step(True)
+    ms = _events_ms(lambda: step(True), n)
+    R.check_deferred()
     with torch.no_grad():
         ms_fwd = _events_ms(lambda: autograd.render(t["means"], t["log_scales"], t["quats"],
-                                                    t["opacity_logits"], t["sh"], 3, R), 5)
+                                                    t["opacity_logits"], t["sh"], 3, R, deferred=True), 5)
+        R.check_deferred()
     return {"workload": "1M-splat cluster scene, SH degree 3, 1024x1024, f1 + opacity cull, L1 loss",
             "ms_forward_backward": ms, "ms_forward": ms_fwd, "steps_per_s": 1e3 / ms,
-            "note": "forward includes the overlap-count read-back of Rasterizer.forward"}
+            "ms_forward_backward_sync_check": ms_sync,
+            "note": "overlap capacity checked one step late (Rasterizer.forward deferred=True); "
+                    "sync_check: read back after every forward, as 3DGS does"}
 
 
 def bench_fp16x2(a):

@@ -208,7 +208,10 @@ gs_status gs_render(void *stream, const gs_camera *cams, int32_t ncam, int32_t P
  * buffers are ACCUMULATED into (the caller zeroes them): d_grad_means [P][3],
  * d_grad_scales [P][3], d_grad_quats [P][4] (for the quaternion as given,
  * before normalisation), d_grad_opacities [P], d_grad_sh [P][(d+1)^2][3].
- * d_grad2d: scratch of gs_grad2d_bytes(ncam, P) bytes (zeroed by the call). */
+ * d_grad2d: scratch of gs_grad2d_bytes(ncam, P) bytes (zeroed by the call).
+ * Tiles of up to 512 pixels (two pixels per thread); larger tiles, and a
+ * forward run with fp16x2 or tensor_alpha (whose skip / stop decisions the
+ * FP32 reverse pass could not reproduce), return GS_ERR_UNSUPPORTED. */
 size_t gs_grad2d_bytes(int32_t ncam, int32_t P);
 gs_status gs_render_backward(void *stream, const gs_camera *cams, int32_t ncam, int32_t P,
                              const gs_config *cfg, const float *d_means,
@@ -251,6 +254,13 @@ gs_status gs_bin_sort_noalloc(void *stream, const gs_camera *cams, int32_t ncam,
  * workspace into *code (OR of GS_ERR_CAPACITY / GS_ERR_TIMEOUT) and clears
  * it. Returns GS_ERR_CUDA if the copy fails. */
 gs_status gs_workspace_status(void *stream, void *d_workspace, int32_t *code);
+
+/* Non-blocking form of gs_workspace_status: enqueues on `stream` a copy of
+ * the error word (one uint32) to dst, then clears the word. dst may be
+ * device memory or pinned host memory; it holds the value once the stream
+ * reaches this point (wait on an event recorded after the call). Returns
+ * GS_ERR_ARG for a null pointer, GS_ERR_CUDA if a copy cannot be enqueued. */
+gs_status gs_workspace_status_async(void *stream, void *d_workspace, uint32_t *dst);
 
 /* Self-test of the bounded waits (failure detection without a fault; not
  * part of the rendering path). Runs one of the two decoupled look-back

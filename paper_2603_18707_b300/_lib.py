@@ -67,6 +67,7 @@ _SIGS = {
                                   C.POINTER(C.c_float), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                   _vp]),
     "gs_workspace_status": (_i32, [_vp, _vp, C.POINTER(_i32)]),
+    "gs_workspace_status_async": (_i32, [_vp, _vp, _vp]),
     "gs_fma_peak": (_i32, [_vp, _i32, _i32, _i32, _vp, C.POINTER(C.c_double)]),
     "gs_selftest_lookback_timeout": (_i32, [_vp, _i32, _vp, _i32]),
     "gs_launch_count": (C.c_uint64, []),

@@ -171,6 +171,13 @@ def gs_workspace_status(workspace, stream=None) -> int:
     return int(code.value)
 
 
+def gs_workspace_status_async(workspace, dst, stream=None) -> None:
+    """Enqueues a copy of the workspace's error word into dst (a 4-byte
+    device or pinned host tensor) and clears the word, without waiting."""
+    check("gs_workspace_status_async", lib().gs_workspace_status_async(_stream(stream), _p(workspace),
+                                                                       _p(dst)))
+
+
 def gs_selftest_lookback_timeout(which: int, scratch, spin_limit: int, stream=None) -> None:
     """Runs a look-back against a predecessor that never publishes (which 0:
     scalar, 1: per digit); the error word scratch[0] then holds

@@ -20,11 +20,12 @@ class RenderFunction(torch.autograd.Function):
     reads: run backward before the next forward on the same rasterizer."""
 
     @staticmethod
-    def forward(ctx, means, scales, quats, opacities, sh, rasterizer: Rasterizer, sh_degree: int, bg):
+    def forward(ctx, means, scales, quats, opacities, sh, rasterizer: Rasterizer, sh_degree: int, bg,
+                deferred: bool = False):
         sc = {"means": means.contiguous(), "scales": scales.contiguous(),
               "quats": quats.contiguous(), "opacities": opacities.contiguous(),
               "sh": sh.contiguous(), "sh_degree": int(sh_degree)}
-        out = rasterizer.forward(sc, bg, n_eval=False)
+        out = rasterizer.forward(sc, bg, n_eval=False, deferred=deferred)
         ctx.rasterizer = rasterizer
         ctx.sh_degree = int(sh_degree)
         ctx.bg = tuple(float(v) for v in bg)
@@ -44,10 +45,15 @@ class RenderFunction(torch.autograd.Function):
                                ctx.sh_degree, R.splat2d, R.vals, R.ranges, ctx.bg, R.final_T,
                                R.last, grad_out.contiguous(), grad2d, g["means"], g["scales"],
                                g["quats"], g["opacities"], g["sh"])
-        return g["means"], g["scales"], g["quats"], g["opacities"], g["sh"], None, None, None
+        return g["means"], g["scales"], g["quats"], g["opacities"], g["sh"], None, None, None, None
 
 
-def render(means, log_scales, quats, opacity_logits, sh, sh_degree, rasterizer, bg=(0.0, 0.0, 0.0)):
-    """Differentiable render from raw 3DGS parameters."""
+def render(means, log_scales, quats, opacity_logits, sh, sh_degree, rasterizer, bg=(0.0, 0.0, 0.0),
+           deferred: bool = False):
+    """Differentiable render from raw 3DGS parameters. deferred=True checks
+    the overlap capacity one call late instead of waiting for the GPU
+    (Rasterizer.forward): a training step then never stalls on a read-back,
+    and the rare step that overflowed raises render.CapacityOverflow at the
+    next call, with the buffers already grown."""
     return RenderFunction.apply(means, torch.exp(log_scales), quats, torch.sigmoid(opacity_logits),
-                                sh, rasterizer, sh_degree, bg)
+                                sh, rasterizer, sh_degree, bg, deferred)

@@ -10,8 +10,10 @@
 //   alpha = o' k(Q) unclamped: dL/do' = k dL/dalpha, dL/dQ = o' k'(Q) dL/dalpha,
 //   k' = -k/2 (exp), c1 + 2 c2 Q + 3 c3 Q^2 (polynomials; the ReLU / cut are
 //   inactive wherever alpha >= eps), then dQ to the conic and the 2D mean.
-// The warp sums its lanes' contributions with shuffles and one lane adds them
-// to the record's 2D gradient with FP32 atomics.
+// Each warp walks the list only up to its own furthest last contributor,
+// sums its lanes' contributions to an entry with shuffles and adds the sums
+// to shared-memory accumulators of the batch; after the batch one thread per
+// entry adds the tile's sums to the record's 2D gradient with FP32 atomics.
 //
 // Stage 2, per splat (one thread, loop over cameras): the chain rule through
 // the projection written in preprocess.cu: colour clamp and SH (and the view
@@ -73,7 +75,22 @@ __device__ __forceinline__ int wsum8_index(int lane)
     return ((lane & 16) ? 4 : 0) + ((lane & 8) ? 2 : 0) + ((lane & 4) ? 1 : 0);
 }
 
-template <int KIND>
+// Shared-memory accumulators of the per-entry gradient sums of one batch:
+// [value][entry] with a row stride of 257 floats, so that the 9 lanes that
+// add one entry's 9 sums hit 9 different banks.
+constexpr int kAccStride = 257;
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// PPT horizontally adjacent pixels per thread (1 or 2): the per-entry setup
+// (shared-memory loads, the row terms of the quadric) and the warp reduction
+// are shared by all of a warp's 32 PPT pixels.
+template <int KIND, int PPT>
 __global__ void __launch_bounds__(256)
 blend_backward_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
                       const float4 *__restrict__ rec, const uint32_t *__restrict__ vals,
@@ -81,12 +98,13 @@ blend_backward_kernel(const __grid_constant__ CamTable cams, const __grid_consta
                       float bg2, const float *__restrict__ final_T, const uint32_t *__restrict__ last,
                       const float *__restrict__ grad_out, float *__restrict__ grad2d)
 {
-    __shared__ float4 s_g[256];
+    __shared__ float4 s_g[256]; // mu'x, mu'y, o', 1 / o'
     __shared__ float4 s_q[256];
     __shared__ float4 s_ka[256];
     __shared__ float4 s_kb[256];
     __shared__ float4 s_kc[256];
     __shared__ uint32_t s_id[256];
+    __shared__ float s_acc[9 * kAccStride];
     __shared__ uint32_t s_maxL;
     const int gtile = blockIdx.x;
     int c = 0;
@@ -94,34 +112,49 @@ blend_backward_kernel(const __grid_constant__ CamTable cams, const __grid_consta
     const CamDev &cm = cams.cam[c];
     const int lt = gtile - cm.tile_base;
     const int tx = lt % cm.tiles_x, ty = lt / cm.tiles_x;
-    const int px = tx * cfg.tile_w + (int)threadIdx.x % cfg.tile_w;
-    const int py = ty * cfg.tile_h + (int)threadIdx.x / cfg.tile_w;
-    const bool inside = px < cm.W && py < cm.H;
-    const float pxc = px + 0.5f, pyc = py + 0.5f;
+    const int tpr = cfg.tile_w / PPT; // threads per tile row
+    const int lx = ((int)threadIdx.x % tpr) * PPT, ly = (int)threadIdx.x / tpr;
+    const int px0 = tx * cfg.tile_w + lx, py = ty * cfg.tile_h + ly;
+    const float pyc = py + 0.5f;
     const float ox = (float)(tx * cfg.tile_w), oy = (float)(ty * cfg.tile_h);
-    const float xl = (float)((int)threadIdx.x % cfg.tile_w) + 0.5f;
-    const float yl = (float)((int)threadIdx.x / cfg.tile_w) + 0.5f;
+    const float yl = (float)ly + 0.5f;
     const uint2 rg = ranges[gtile];
     const int lane = threadIdx.x & 31;
 
-    float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    uint32_t L = 0;
-    if (inside) {
-        const int64_t pix = cm.pix_base + (int64_t)py * cm.W + px;
-        T = final_T[pix];
-        L = last[pix];
-        g0 = grad_out[3 * pix + 0];
-        g1 = grad_out[3 * pix + 1];
-        g2 = grad_out[3 * pix + 2];
+    float T[PPT], S[PPT][3], gr[PPT][3], xl[PPT];
+    uint32_t L[PPT];
+    uint32_t Lmax = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        T[k] = 1.f;
+        L[k] = 0;
+        gr[k][0] = gr[k][1] = gr[k][2] = 0.f;
+        xl[k] = (float)(lx + k) + 0.5f;
+        if (px0 + k < cm.W && py < cm.H) {
+            const int64_t pix = cm.pix_base + (int64_t)py * cm.W + px0 + k;
+            T[k] = final_T[pix];
+            L[k] = last[pix];
+            gr[k][0] = grad_out[3 * pix + 0];
+            gr[k][1] = grad_out[3 * pix + 1];
+            gr[k][2] = grad_out[3 * pix + 2];
+        }
+        S[k][0] = T[k] * bg0;
+        S[k][1] = T[k] * bg1;
+        S[k][2] = T[k] * bg2;
+        Lmax = max(Lmax, L[k]);
     }
-    float S0 = T * bg0, S1 = T * bg1, S2 = T * bg2;
     if (threadIdx.x == 0) s_maxL = 0;
+    for (int k = threadIdx.x; k < 9 * kAccStride; k += blockDim.x) s_acc[k] = 0.f;
     __syncthreads();
-    if (L) atomicMax(&s_maxL, L);
+    if (Lmax) atomicMax(&s_maxL, Lmax);
     __syncthreads();
     // a pixel's last lies within its tile list (an inverted range, only
     // possible after a timed-out sort wait, counts as empty)
-    const int maxL = (int)min(s_maxL, rg.y > rg.x ? rg.y - rg.x : 0u);
+    const uint32_t n = rg.y > rg.x ? rg.y - rg.x : 0u;
+    const int maxL = (int)min(s_maxL, n);
+    // this warp's furthest last contributor: entries beyond it touch none of
+    // its pixels
+    const int wL = (int)min(__reduce_max_sync(0xffffffffu, Lmax), n);
     const int B = blockDim.x;
     const float eps = cfg.eps, amax = cfg.alpha_max;
     for (int end = maxL; end > 0; end -= B) {
@@ -133,61 +166,88 @@ blend_backward_kernel(const __grid_constant__ CamTable cams, const __grid_consta
             s_id[threadIdx.x] = v;
             const float4 r0 = rec[3 * (size_t)v + 0], r1 = rec[3 * (size_t)v + 1];
             const BlendCoef kc = make_coef<KIND>(cfg, r0, r1, rec[3 * (size_t)v + 2], ox, oy);
-            s_g[threadIdx.x] = r0;
+            s_g[threadIdx.x] = make_float4(r0.x, r0.y, r0.z, 1.f / r0.z);
             s_q[threadIdx.x] = r1;
             s_ka[threadIdx.x] = kc.a;
             s_kb[threadIdx.x] = kc.b;
             s_kc[threadIdx.x] = kc.c;
         }
         __syncthreads();
-        for (int j = end - 1; j >= start; --j) {
+        for (int j = min(end, wL) - 1; j >= start; --j) {
             const int jj = j - start;
             // alpha exactly as the forward computed it
             const float4 ka = s_ka[jj], kb = s_kb[jj];
-            const float u = fmaf(ka.x, xl, fmaf(ka.y, yl, ka.z));
+            const float p3 = (KIND == GS_K_POLY3) ? s_kc[jj].w : 0.f;
+            const float ub = fmaf(ka.y, yl, ka.z);
             const float vv = fmaf(ka.w, yl, kb.x);
-            const float Q = fmaf(u, u, vv * vv);
-            const float a0 = alpha_of_q<KIND>(cfg, kb, s_kc[jj].w, Q);
-            const float a = fminf(amax, a0);
-            const bool contrib = (uint32_t)j < L && a >= eps;
+            const float v2 = vv * vv;
+            float Q[PPT], a0[PPT];
+            bool con[PPT], anyc = false;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                const float u = fmaf(ka.x, xl[k], ub);
+                Q[k] = fmaf(u, u, v2);
+                a0[k] = alpha_of_q<KIND>(cfg, kb, p3, Q[k]);
+                con[k] = (uint32_t)j < L[k] && fminf(amax, a0[k]) >= eps;
+                anyc |= con[k];
+            }
+            if (!__any_sync(0xffffffffu, anyc)) continue;
+            const float4 g = s_g[jj];
+            const float4 q = s_q[jj];
+            const float4 col = s_kc[jj];
+            const float dy = g.y - pyc;
             float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (contrib) {
-                const float4 g = s_g[jj];
-                const float4 q = s_q[jj];
-                const float dx = g.x - pxc, dy = g.y - pyc;
-                const float4 col = s_kc[jj];
-                const float oma = 1.f - a;
-                T = T / oma;
-                const float w = a * T;
-                v[6] = w * g0;
-                v[7] = w * g1;
-                v[8] = w * g2;
-                const float ioma = 1.f / oma;
-                const float da = g0 * (col.x * T - S0 * ioma) + g1 * (col.y * T - S1 * ioma) +
-                                 g2 * (col.z * T - S2 * ioma);
-                S0 = fmaf(col.x, w, S0);
-                S1 = fmaf(col.y, w, S1);
-                S2 = fmaf(col.z, w, S2);
-                if (a0 <= amax) {
-                    v[5] = a0 / g.z * da; // k(Q) = o' k(Q) / o'
-                    const float dQ = g.z * kernel_slope<KIND>(cfg, Q, a0, g.z) * da;
-                    v[2] = dQ * dx * dx;
-                    v[3] = dQ * 2.f * dx * dy;
-                    v[4] = dQ * dy * dy;
-                    v[0] = dQ * 2.f * (q.x * dx + q.y * dy);
-                    v[1] = dQ * 2.f * (q.y * dx + q.z * dy);
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                if (!con[k]) continue;
+                const float a = fminf(amax, a0[k]);
+                const float ioma = rcp_approx(1.f - a);
+                T[k] *= ioma; // transmittance before this entry
+                const float w = a * T[k];
+                v[6] = fmaf(w, gr[k][0], v[6]);
+                v[7] = fmaf(w, gr[k][1], v[7]);
+                v[8] = fmaf(w, gr[k][2], v[8]);
+                const float da = gr[k][0] * (col.x * T[k] - S[k][0] * ioma) +
+                                 gr[k][1] * (col.y * T[k] - S[k][1] * ioma) +
+                                 gr[k][2] * (col.z * T[k] - S[k][2] * ioma);
+                S[k][0] = fmaf(col.x, w, S[k][0]);
+                S[k][1] = fmaf(col.y, w, S[k][1]);
+                S[k][2] = fmaf(col.z, w, S[k][2]);
+                if (a0[k] <= amax) {
+                    v[5] = fmaf(a0[k] * g.w, da, v[5]); // k(Q) = o' k(Q) / o'
+                    // o' dk/dQ: -o' k / 2 for exp, o' k'(Q) for the polynomials
+                    const float dQ =
+                        (KIND == GS_K_EXP ? -0.5f * a0[k] : g.z * kernel_slope<KIND>(cfg, Q[k], a0[k], g.z)) * da;
+                    const float dx = g.x - (float)(px0 + k) - 0.5f;
+                    const float dQx = dQ * dx, dQy = dQ * dy;
+                    v[2] = fmaf(dQx, dx, v[2]);
+                    v[3] = fmaf(2.f * dQx, dy, v[3]);
+                    v[4] = fmaf(dQy, dy, v[4]);
+                    v[0] = fmaf(2.f * dQ, fmaf(q.x, dx, q.y * dy), v[0]);
+                    v[1] = fmaf(2.f * dQ, fmaf(q.y, dx, q.z * dy), v[1]);
                 }
             }
-            if (__any_sync(0xffffffffu, contrib)) {
-                const float v8[8] = {v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7]};
-                const float s8 = wsum8(v8, lane);
-                const float s9 = wsum(v[8]);
-                float *dst = grad2d + (size_t)s_id[jj] * kG2;
-                if ((lane & 3) == 0 && s8 != 0.f) atomicAdd(dst + wsum8_index(lane), s8);
-                if (lane == 1 && s9 != 0.f) atomicAdd(dst + 8, s9);
-            }
+            const float v8[8] = {v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7]};
+            const float s8 = wsum8(v8, lane);
+            const float s9 = wsum(v[8]);
+            if ((lane & 3) == 0 && s8 != 0.f) atomicAdd(&s_acc[wsum8_index(lane) * kAccStride + jj], s8);
+            if (lane == 1 && s9 != 0.f) atomicAdd(&s_acc[8 * kAccStride + jj], s9);
         }
         __syncthreads();
+        // one set of global atomics per entry and tile; each thread flushes
+        // (and clears) the entry it staged, so the next batch's staging by
+        // the same thread needs no further barrier
+        if (i < end) {
+            float *dst = grad2d + (size_t)s_id[threadIdx.x] * kG2;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const float sv = s_acc[k * kAccStride + threadIdx.x];
+                if (sv != 0.f) {
+                    atomicAdd(dst + k, sv);
+                    s_acc[k * kAccStride + threadIdx.x] = 0.f;
+                }
+            }
+        }
     }
 }
 
@@ -246,19 +306,23 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float *
     }
 }
 
+// Chain rule of one splat through its projections (all cameras). sh_row:
+// the splat's 3K SH coefficients; dsh: its SH gradient accumulators, one
+// every dstride floats.
 template <int D>
-__global__ void __launch_bounds__(128)
-project_backward_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
-                        int P, const float *__restrict__ means, const float *__restrict__ scales,
-                        const float *__restrict__ quats, const float *__restrict__ opacities,
-                        const float *__restrict__ sh, const float *__restrict__ grad2d,
-                        float *__restrict__ g_means, float *__restrict__ g_scales,
-                        float *__restrict__ g_quats, float *__restrict__ g_opac,
-                        float *__restrict__ g_sh)
+__device__ __forceinline__ void project_backward_splat(const CamTable &cams, const CfgDev &cfg, int P, int i,
+                                                       const float *__restrict__ means,
+                                                       const float *__restrict__ scales,
+                                                       const float *__restrict__ quats,
+                                                       const float *__restrict__ opacities,
+                                                       const float *sh_row, float *dsh, int dstride,
+                                                       const float *__restrict__ grad2d,
+                                                       float *__restrict__ g_means,
+                                                       float *__restrict__ g_scales,
+                                                       float *__restrict__ g_quats,
+                                                       float *__restrict__ g_opac)
 {
     constexpr int K = (D + 1) * (D + 1);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P) return;
     const float mx = means[3 * i + 0], my = means[3 * i + 1], mz = means[3 * i + 2];
     const float sx = scales[3 * i + 0], sy = scales[3 * i + 1], sz = scales[3 * i + 2];
     const float4 q4 = reinterpret_cast<const float4 *>(quats)[i];
@@ -282,9 +346,6 @@ project_backward_kernel(const __grid_constant__ CamTable cams, const __grid_cons
 
     float dmean[3] = {0.f, 0.f, 0.f}, dSig[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     float dop = 0.f;
-    float dsh[K * 3];
-#pragma unroll
-    for (int k = 0; k < K * 3; ++k) dsh[k] = 0.f;
     bool any = false;
 
     for (int c = 0; c < cams.ncam; ++c) {
@@ -337,7 +398,7 @@ project_backward_kernel(const __grid_constant__ CamTable cams, const __grid_cons
         for (int ch = 0; ch < 3; ++ch) {
             float acc = 0.f;
 #pragma unroll
-            for (int k = 0; k < K; ++k) acc = fmaf(Y[k], sh[((size_t)i * K + k) * 3 + ch], acc);
+            for (int k = 0; k < K; ++k) acc = fmaf(Y[k], sh_row[3 * k + ch], acc);
             draw[ch] = (acc + 0.5f > 0.f) ? dcol[ch] : 0.f;
         }
         float ddir[3] = {0.f, 0.f, 0.f};
@@ -346,8 +407,8 @@ project_backward_kernel(const __grid_constant__ CamTable cams, const __grid_cons
             float t = 0.f;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
-                dsh[3 * k + ch] = fmaf(Y[k], draw[ch], dsh[3 * k + ch]);
-                t = fmaf(sh[((size_t)i * K + k) * 3 + ch], draw[ch], t);
+                dsh[(3 * k + ch) * dstride] = fmaf(Y[k], draw[ch], dsh[(3 * k + ch) * dstride]);
+                t = fmaf(sh_row[3 * k + ch], draw[ch], t);
             }
             ddir[0] = fmaf(GY[k][0], t, ddir[0]);
             ddir[1] = fmaf(GY[k][1], t, ddir[1]);
@@ -445,8 +506,51 @@ project_backward_kernel(const __grid_constant__ CamTable cams, const __grid_cons
         g_scales[3 * i + k] += ds[k];
     }
     g_opac[i] += dop;
-#pragma unroll
-    for (int k = 0; k < K * 3; ++k) g_sh[(size_t)i * K * 3 + k] += dsh[k];
+}
+
+// Splats per CTA of the per-splat pass. The CTA stages its splats' SH rows
+// in shared memory with coalesced loads (row stride 3K + 1 floats, odd, so a
+// warp reading one coefficient of 32 rows hits 32 banks) and accumulates the
+// SH gradients there ([coefficient][splat], stride kPB + 1), then adds them
+// to the caller's buffer with coalesced read-modify-writes.
+constexpr int kPB = 64;
+
+template <int D>
+__global__ void __launch_bounds__(kPB, 8)
+project_backward_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
+                        int P, const float *__restrict__ means, const float *__restrict__ scales,
+                        const float *__restrict__ quats, const float *__restrict__ opacities,
+                        const float *__restrict__ sh, const float *__restrict__ grad2d,
+                        float *__restrict__ g_means, float *__restrict__ g_scales,
+                        float *__restrict__ g_quats, float *__restrict__ g_opac,
+                        float *__restrict__ g_sh)
+{
+    constexpr int K = (D + 1) * (D + 1);
+    constexpr int F = 3 * K, FS = F + 1, DS = kPB + 1;
+    __shared__ float s_sh[kPB * FS];
+    __shared__ float s_dsh[F * DS];
+    const int i0 = blockIdx.x * kPB;
+    const int nb = min(kPB, P - i0);
+    {
+        const float *src = sh + (size_t)i0 * F;
+        for (int idx = threadIdx.x; idx < nb * F; idx += kPB) {
+            const int r = idx / F;
+            s_sh[r * FS + idx - r * F] = src[idx];
+        }
+        for (int k = threadIdx.x; k < F * DS; k += kPB) s_dsh[k] = 0.f;
+    }
+    __syncthreads();
+    const int i = i0 + (int)threadIdx.x;
+    if (i < P) project_backward_splat<D>(cams, cfg, P, i, means, scales, quats, opacities,
+                                         s_sh + threadIdx.x * FS, s_dsh + threadIdx.x, DS, grad2d,
+                                         g_means, g_scales, g_quats, g_opac);
+    __syncthreads();
+    float *dst = g_sh + (size_t)i0 * F;
+    for (int idx = threadIdx.x; idx < nb * F; idx += kPB) {
+        const int r = idx / F;
+        const float v = s_dsh[(idx - r * F) * DS + r];
+        if (v != 0.f) dst[idx] += v;
+    }
 }
 
 } // namespace
@@ -484,7 +588,7 @@ extern "C" gs_status gs_render_backward(void *stream, const gs_camera *cams, int
     CamTable t;
     CfgDev c;
     if (!build_cam_table(cams, ncam, cfg, &t) || !build_cfg(cfg, &c)) return GS_ERR_ARG;
-    if (cfg->tile_w * cfg->tile_h > 256) return GS_ERR_UNSUPPORTED;
+    if (cfg->tile_w * cfg->tile_h > 512) return GS_ERR_UNSUPPORTED; // 256 threads of two pixels
     // the reverse pass recomputes alpha in FP32; an FP16x2 forward could have
     // taken different skip / stop decisions
     if (cfg->fp16x2 || cfg->tensor_alpha) return GS_ERR_UNSUPPORTED;
@@ -494,21 +598,31 @@ extern "C" gs_status gs_render_backward(void *stream, const gs_camera *cams, int
     const float4 *rec = splat2d_const(d_splat2d, N).rec;
     const uint2 *rg = reinterpret_cast<const uint2 *>(d_ranges);
     float *g2 = static_cast<float *>(d_grad2d);
-    const int threads = cfg->tile_w * cfg->tile_h;
-#define GS_BWD_LAUNCH(K)                                                                             \
-    blend_backward_kernel<K><<<t.total_tiles, threads, 0, s>>>(t, c, rec, d_vals, rg, (uint32_t)N,   \
-                                                               bg[0], bg[1], bg[2], d_final_T,       \
-                                                               d_last, d_grad_out, g2)
-    switch (cfg->kind) {
-    case GS_K_EXP: GS_BWD_LAUNCH(GS_K_EXP); break;
-    case GS_K_POLY1: GS_BWD_LAUNCH(GS_K_POLY1); break;
-    case GS_K_POLY2: GS_BWD_LAUNCH(GS_K_POLY2); break;
-    default: GS_BWD_LAUNCH(GS_K_POLY3); break;
+    // two pixels per thread (tile widths are even; one per thread otherwise)
+    const int ppt = (cfg->tile_w % 2 == 0) ? 2 : 1;
+    if (cfg->tile_w * cfg->tile_h / ppt > 256) return GS_ERR_UNSUPPORTED;
+    const int threads = cfg->tile_w * cfg->tile_h / ppt;
+#define GS_BWD_LAUNCH(K, PP)                                                                         \
+    blend_backward_kernel<K, PP><<<t.total_tiles, threads, 0, s>>>(t, c, rec, d_vals, rg, (uint32_t)N, \
+                                                                   bg[0], bg[1], bg[2], d_final_T,   \
+                                                                   d_last, d_grad_out, g2)
+#define GS_BWD_KIND(PP)                                                                              \
+    switch (cfg->kind) {                                                                             \
+    case GS_K_EXP: GS_BWD_LAUNCH(GS_K_EXP, PP); break;                                               \
+    case GS_K_POLY1: GS_BWD_LAUNCH(GS_K_POLY1, PP); break;                                           \
+    case GS_K_POLY2: GS_BWD_LAUNCH(GS_K_POLY2, PP); break;                                           \
+    default: GS_BWD_LAUNCH(GS_K_POLY3, PP); break;                                                   \
     }
+    if (ppt == 2) {
+        GS_BWD_KIND(2)
+    } else {
+        GS_BWD_KIND(1)
+    }
+#undef GS_BWD_KIND
 #undef GS_BWD_LAUNCH
     count_launch();
     GS_LAUNCH_CHECK();
-    const int pt = 128, pb = (P + pt - 1) / pt;
+    const int pt = kPB, pb = (P + pt - 1) / pt;
 #define GS_PBWD_LAUNCH(D)                                                                          \
     project_backward_kernel<D><<<pb, pt, 0, s>>>(t, c, P, d_means, d_scales, d_quats, d_opacities, \
                                                  d_sh, g2, d_grad_means, d_grad_scales,            \

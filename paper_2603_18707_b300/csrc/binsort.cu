@@ -925,6 +925,17 @@ extern "C" gs_status gs_workspace_status(void *stream, void *d_workspace, int32_
     return GS_OK;
 }
 
+extern "C" gs_status gs_workspace_status_async(void *stream, void *d_workspace, uint32_t *dst)
+{
+    if (!d_workspace || !dst) return GS_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    WsHeader *hdr = reinterpret_cast<WsHeader *>(d_workspace);
+    if (cudaMemcpyAsync(dst, &hdr->err, sizeof(uint32_t), cudaMemcpyDefault, s) != cudaSuccess)
+        return GS_ERR_CUDA;
+    if (cudaMemsetAsync(&hdr->err, 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
+    return GS_OK;
+}
+
 // Self-test of the bounded waits (fault injection without a fault): the two
 // look-back routines above run against a predecessor that never publishes
 // (all-zero flags in d_scratch). They must give up after `limit` sleeps,

@@ -16,6 +16,11 @@ from ._lib import GS_ERR_CAPACITY
 MAX_CAPACITY = (1 << 30) - 2  # the binning's counters hold 30 bits (< 2^30 - 1 overlaps)
 
 
+class CapacityOverflow(RuntimeError):
+    """A deferred pass had more tile overlaps than the buffers held; they
+    have been grown, and the pass should be repeated."""
+
+
 def activate(scene: dict, device="cuda") -> dict:
     """3DGS activations of raw parameters: scale = exp(log-scale), opacity =
     sigmoid(logit). Means, quaternions (normalised inside the library) and SH
@@ -58,6 +63,11 @@ class Rasterizer:
         self.work = (torch.zeros(api.gs_render_work_bytes(), **u8) if persistent else None)
         self.shrink = capacity is None  # an explicit capacity is kept as given
         self.capacity = 0
+        self.sized = False  # a synchronous forward() has fitted the capacity
+        self.overflows = 0  # deferred passes found to have exceeded the capacity
+        self._pending = None
+        self._status_dev = torch.zeros(4, **i32)
+        self._status_host = torch.zeros(4, dtype=torch.int32).pin_memory() if self.device.type == "cuda" else None
         self._alloc(capacity if capacity else min(max(1 << 20, 8 * self.ncam * self.P), MAX_CAPACITY))
 
     def _alloc(self, capacity: int):
@@ -82,10 +92,30 @@ class Rasterizer:
                       self.out, self.final_T, self.last, self.n_eval if n_eval else None,
                       self.work)
 
-    def forward(self, sc: dict, bg=(0.0, 0.0, 0.0), n_eval: bool = True):
+    def forward(self, sc: dict, bg=(0.0, 0.0, 0.0), n_eval: bool = True, deferred: bool = False):
         """One pass of the whole path; grows the overlap buffer when it was
         too small and shrinks it when it is far too large (the sort's grids
-        and look-back state scale with the capacity), then reruns."""
+        and look-back state scale with the capacity), then reruns.
+
+        deferred=True (once a synchronous pass has sized the buffers) runs the
+        pass without waiting for the GPU: the device error word and the
+        overlap count are copied to pinned host memory behind the pass and
+        checked at the next deferred call, so a training loop never stalls
+        the GPU on a read-back. A pass that overflowed the capacity (its
+        image and gradients miss the overlaps beyond it) is found one call
+        later: that call grows the buffers, counts it in `overflows` and
+        raises CapacityOverflow, so the caller can repeat the step."""
+        if deferred and self.sized:
+            self.check_deferred()
+            self.run_async(sc, bg, n_eval)
+            api.gs_workspace_status_async(self.workspace, self._status_dev[0:1])
+            self._status_dev[1:4].copy_(self.count)
+            self._status_host.copy_(self._status_dev, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record()
+            self._pending = ev
+            return self.out
+        self._pending = None
         for _ in range(4):
             self.preprocess(sc)
             self.bin_sort()
@@ -98,11 +128,30 @@ class Rasterizer:
                 if self.shrink and self.capacity > 2 * need + (1 << 16):
                     self._alloc(int(need * 1.15) + 4096)
                     continue
+                self.sized = True
                 return self.out
             if self.capacity >= MAX_CAPACITY:
                 raise RuntimeError("more than 2^30 - 1 tile overlaps: split the camera batch")
             self._alloc(min(int(max(need, self.capacity) * 1.25) + 1024, MAX_CAPACITY))
         raise RuntimeError("overlap capacity could not be sized")
+
+    def check_deferred(self):
+        """Waits for the last deferred pass's status copy (normally long
+        complete) and raises CapacityOverflow, after growing the buffers, if
+        that pass exceeded the overlap capacity."""
+        ev, self._pending = self._pending, None
+        if ev is None:
+            return
+        ev.synchronize()
+        err, need = int(self._status_host[0]), int(self._status_host[3]) & 0xFFFFFFFF
+        if err & GS_ERR_CAPACITY:
+            self.overflows += 1
+            if self.capacity >= MAX_CAPACITY:
+                raise RuntimeError("more than 2^30 - 1 tile overlaps: split the camera batch")
+            self._alloc(min(int(max(need, self.capacity) * 1.25) + 1024, MAX_CAPACITY))
+            raise CapacityOverflow(f"the previous pass needed {need} overlaps; capacity grown to {self.capacity}")
+        if err:
+            raise RuntimeError(f"device error word {err}")
 
     def run_async(self, sc: dict, bg=(0.0, 0.0, 0.0), n_eval: bool = False):
         """The same pass without any host synchronisation (for timing and
@@ -192,9 +241,9 @@ class StreamedRasterizer:
         for r in self.parts:
             r.blend(bg, n_eval)
 
-    def forward(self, sc: dict, bg=(0.0, 0.0, 0.0), n_eval: bool = True):
+    def forward(self, sc: dict, bg=(0.0, 0.0, 0.0), n_eval: bool = True, deferred: bool = False):
         for r in self.parts:
-            r.forward(sc, bg, n_eval)
+            r.forward(sc, bg, n_eval, deferred)
         return self.out
 
     def run_async(self, sc: dict, bg=(0.0, 0.0, 0.0), n_eval: bool = False):

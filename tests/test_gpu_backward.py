@@ -147,6 +147,29 @@ def test_autograd_function_chains_activations(gs):
     assert np.allclose(t["sh"].grad.cpu().numpy(), gpu["sh"], rtol=1e-5, atol=1e-7)
 
 
+def test_autograd_deferred_check_matches_synchronous(gs):
+    """The training-loop mode (capacity checked one call late) gives the
+    gradients of the synchronous mode."""
+    api, render, synth = gs
+    from paper_2603_18707_b300 import autograd
+    raw = _small_scene()
+    cam = synth.look_at([0.3, -0.2, -2.5], [0, 0, 0], 56, 48, 60.0)
+    R = render.Rasterizer([cam], api.make_config("poly1", "opacity"), 48)
+    w = torch.randn(48 * 56, 3, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+    grads = []
+    for deferred in (False, True, True):
+        t = {k: torch.tensor(raw[k], device="cuda", requires_grad=True)
+             for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+        img = autograd.render(t["means"], t["log_scales"], t["quats"], t["opacity_logits"], t["sh"], 3, R,
+                              deferred=deferred)
+        (img * w).sum().backward()
+        grads.append({k: v.grad.clone() for k, v in t.items()})
+    R.check_deferred()
+    for g in grads[1:]:
+        for k in g:
+            assert torch.allclose(g[k], grads[0][k], rtol=1e-5, atol=1e-8), k
+
+
 def test_differentiable_1M_scene_sampled_tiles(gs, orc):
     """1M-splat cluster scene at 1024x1024: L1 loss against the render of a
     perturbed copy. The full gradient is finite; with the loss restricted to

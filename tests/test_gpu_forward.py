@@ -292,6 +292,35 @@ def test_capacity_overflow_is_reported_and_recovered(gs, small):
     assert api.gs_workspace_status(R.workspace) == 0
 
 
+def test_deferred_capacity_check(gs, small):
+    """forward(deferred=True) renders exactly what the synchronous pass
+    renders, and a deferred pass that overflows the capacity is reported by
+    the next call (CapacityOverflow, buffers grown); the repeated pass is
+    exact again."""
+    from paper_2603_18707_b300 import api, render, synth
+    cam = synth.camera_small()
+    cfg = api.make_config("poly1", "opacity")
+    sc = render.activate(small)
+    ref = _gpu(gs, small, [cam], "poly1", "opacity").images()[0].clone()
+    R = render.Rasterizer([cam], cfg, 4096)
+    R.forward(sc, deferred=True)  # not sized yet: synchronous
+    assert R.sized and torch.equal(R.images()[0], ref)
+    for _ in range(3):
+        R.forward(sc, deferred=True)
+    R.check_deferred()
+    assert torch.equal(R.images()[0], ref) and R.overflows == 0
+    need = R.n_records()[1]
+    R._alloc(need // 2)
+    R.forward(sc, deferred=True)  # overflows; not known yet
+    with pytest.raises(render.CapacityOverflow):
+        R.forward(sc, deferred=True)
+    assert R.overflows == 1 and R.capacity >= need
+    R.forward(sc, deferred=True)
+    R.check_deferred()
+    assert torch.equal(R.images()[0], ref)
+    assert api.gs_workspace_status(R.workspace) == 0
+
+
 def test_full_size_scene_sampled_tiles(gs, orc):
     """3M-splat cluster scene at 1920x1080 (SH degree 3), camera 0 of the
     orbit, in the launch configuration of the benchmark: 24 sampled tiles
