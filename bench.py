@@ -533,23 +533,40 @@ def bench_differentiable(a):
                               deferred=deferred)
         (img - target).abs().mean().backward()
 
+    def gstep():
+        for v in t.values():
+            v.grad = None
+        img = autograd.render(t["means"], t["log_scales"], t["quats"], t["opacity_logits"], t["sh"], 3, R,
+                              deferred=True)
+        loss = (img - target).abs().mean()
+        loss.backward()
+        return loss
+
     n = max(5, a.steps // 6)
     for _ in range(3):
         step(False)
     ms_sync = _events_ms(lambda: step(False), n)
     for _ in range(3):
         step(True)
-    ms = _events_ms(lambda: step(True), n)
+    ms_eager = _events_ms(lambda: step(True), n)
     R.check_deferred()
+    G = autograd.GraphedStep(gstep, R)
+    for _ in range(3):
+        G()
+    ms = _events_ms(G, n)
+    G.check()
     with torch.no_grad():
         ms_fwd = _events_ms(lambda: autograd.render(t["means"], t["log_scales"], t["quats"],
                                                     t["opacity_logits"], t["sh"], 3, R, deferred=True), 5)
         R.check_deferred()
     return {"workload": "1M-splat cluster scene, SH degree 3, 1024x1024, f1 + opacity cull, L1 loss",
             "ms_forward_backward": ms, "ms_forward": ms_fwd, "steps_per_s": 1e3 / ms,
+            "mode": "autograd.GraphedStep: forward, loss and backward captured as one CUDA graph, "
+                    "overlap capacity checked one replay late",
+            "ms_forward_backward_eager": ms_eager,
             "ms_forward_backward_sync_check": ms_sync,
-            "note": "overlap capacity checked one step late (Rasterizer.forward deferred=True); "
-                    "sync_check: read back after every forward, as 3DGS does"}
+            "note": "eager: the same step launched from Python each time (capacity checked one step "
+                    "late); sync_check: eager with a read-back after every forward, as 3DGS does"}
 
 
 def bench_fp16x2(a):

@@ -10,7 +10,7 @@ from __future__ import annotations
 import torch
 
 from . import api
-from .render import Rasterizer
+from .render import CapacityOverflow, Rasterizer
 
 
 class RenderFunction(torch.autograd.Function):
@@ -57,3 +57,67 @@ def render(means, log_scales, quats, opacity_logits, sh, sh_degree, rasterizer, 
     next call, with the buffers already grown."""
     return RenderFunction.apply(means, torch.exp(log_scales), quats, torch.sigmoid(opacity_logits),
                                 sh, rasterizer, sh_degree, bg, deferred)
+
+
+class GraphedStep:
+    """A whole training step captured once as a CUDA graph and replayed.
+
+    fn() runs one step on tensors that keep their storage: `render(...,
+    deferred=True)` on `rasterizer`, a loss, backward (with the parameters'
+    .grad set to None first, so that the capture allocates them), optionally
+    an optimizer update; it returns what the caller wants to read (e.g. the
+    loss). The step's host work (its ~40 launches, the autograd graph) is
+    paid once at capture; a replay is one graph launch, so the GPU runs the
+    steps back to back. The overlap capacity is checked one replay late from
+    the status the graph copies to pinned host memory: a replay that
+    overflowed raises render.CapacityOverflow at the next call, after the
+    rasterizer's buffers have been grown and the graph captured again, so
+    that the caller can repeat that step."""
+
+    def __init__(self, fn, rasterizer, warmup: int = 3):
+        self.fn, self.R, self.warmup = fn, rasterizer, int(warmup)
+        self._event = None
+        self._capture()
+
+    def _capture(self):
+        self.out = None
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(max(1, self.warmup)):
+                while True:
+                    try:
+                        self.fn()
+                        break
+                    except CapacityOverflow:
+                        continue
+            self.R.check_deferred()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            out = self.fn()
+        # detached views of the static outputs: holding a loss with its
+        # grad_fn would keep the captured autograd graph (and its saved
+        # tensors) alive
+        self.out = out.detach() if isinstance(out, torch.Tensor) else out
+
+    def check(self):
+        """Raises CapacityOverflow (graph recaptured) if the last replay
+        exceeded the overlap capacity."""
+        ev, self._event = self._event, None
+        if ev is None:
+            return
+        try:
+            self.R.check_deferred(ev)
+        except CapacityOverflow:
+            self.graph = None
+            self._capture()
+            raise
+
+    def __call__(self):
+        self.check()
+        self.graph.replay()
+        self._event = torch.cuda.Event()
+        self._event.record()
+        return self.out

@@ -75,10 +75,15 @@ __device__ __forceinline__ int wsum8_index(int lane)
     return ((lane & 16) ? 4 : 0) + ((lane & 8) ? 2 : 0) + ((lane & 4) ? 1 : 0);
 }
 
-// Shared-memory accumulators of the per-entry gradient sums of one batch:
-// [value][entry] with a row stride of 257 floats, so that the 9 lanes that
-// add one entry's 9 sums hit 9 different banks.
-constexpr int kAccStride = 257;
+// Dynamic shared memory of the reverse blend for a batch of B entries (B =
+// threads per CTA): five float4 arrays (2D mean and 1 / o', conic, three
+// coefficient vectors), the record ids, and the accumulators of the
+// per-entry gradient sums, [value][entry] with a row stride of B + 1 floats
+// (odd), so that the 9 lanes that add one entry's 9 sums hit 9 banks.
+__host__ __device__ constexpr size_t bwd_smem_bytes(int B)
+{
+    return (size_t)B * (5 * sizeof(float4) + sizeof(uint32_t)) + sizeof(float) * 9 * (B + 1);
+}
 
 __device__ __forceinline__ float rcp_approx(float x)
 {
@@ -98,13 +103,16 @@ blend_backward_kernel(const __grid_constant__ CamTable cams, const __grid_consta
                       float bg2, const float *__restrict__ final_T, const uint32_t *__restrict__ last,
                       const float *__restrict__ grad_out, float *__restrict__ grad2d)
 {
-    __shared__ float4 s_g[256]; // mu'x, mu'y, o', 1 / o'
-    __shared__ float4 s_q[256];
-    __shared__ float4 s_ka[256];
-    __shared__ float4 s_kb[256];
-    __shared__ float4 s_kc[256];
-    __shared__ uint32_t s_id[256];
-    __shared__ float s_acc[9 * kAccStride];
+    extern __shared__ float4 s_dyn[];
+    const int B = blockDim.x;
+    float4 *s_g = s_dyn; // mu'x, mu'y, o', 1 / o'
+    float4 *s_q = s_g + B;
+    float4 *s_ka = s_q + B;
+    float4 *s_kb = s_ka + B;
+    float4 *s_kc = s_kb + B;
+    uint32_t *s_id = reinterpret_cast<uint32_t *>(s_kc + B);
+    float *s_acc = reinterpret_cast<float *>(s_id + B);
+    const int kAccStride = B + 1;
     __shared__ uint32_t s_maxL;
     const int gtile = blockIdx.x;
     int c = 0;
@@ -155,7 +163,6 @@ blend_backward_kernel(const __grid_constant__ CamTable cams, const __grid_consta
     // this warp's furthest last contributor: entries beyond it touch none of
     // its pixels
     const int wL = (int)min(__reduce_max_sync(0xffffffffu, Lmax), n);
-    const int B = blockDim.x;
     const float eps = cfg.eps, amax = cfg.alpha_max;
     for (int end = maxL; end > 0; end -= B) {
         const int start = max(0, end - B);
@@ -306,27 +313,21 @@ __device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float *
     }
 }
 
-// Chain rule of one splat through its projections (all cameras). sh_row:
-// the splat's 3K SH coefficients; dsh: its SH gradient accumulators, one
-// every dstride floats.
+// Chain rule of one splat through its projections (all cameras). io: the
+// splat's inputs on entry (mean 3, scale 3, quaternion 4, opacity 1), its
+// gradients with respect to them on return; sh_row: its 3K SH coefficients;
+// dsh: its SH gradient accumulators, one every dstride floats.
+constexpr int kIO = 11;
 template <int D>
 __device__ __forceinline__ void project_backward_splat(const CamTable &cams, const CfgDev &cfg, int P, int i,
-                                                       const float *__restrict__ means,
-                                                       const float *__restrict__ scales,
-                                                       const float *__restrict__ quats,
-                                                       const float *__restrict__ opacities,
-                                                       const float *sh_row, float *dsh, int dstride,
-                                                       const float *__restrict__ grad2d,
-                                                       float *__restrict__ g_means,
-                                                       float *__restrict__ g_scales,
-                                                       float *__restrict__ g_quats,
-                                                       float *__restrict__ g_opac)
+                                                       float *io, const float *sh_row, float *dsh,
+                                                       int dstride, const float *__restrict__ grad2d)
 {
     constexpr int K = (D + 1) * (D + 1);
-    const float mx = means[3 * i + 0], my = means[3 * i + 1], mz = means[3 * i + 2];
-    const float sx = scales[3 * i + 0], sy = scales[3 * i + 1], sz = scales[3 * i + 2];
-    const float4 q4 = reinterpret_cast<const float4 *>(quats)[i];
-    const float op = opacities[i];
+    const float mx = io[0], my = io[1], mz = io[2];
+    const float sx = io[3], sy = io[4], sz = io[5];
+    const float4 q4 = make_float4(io[6], io[7], io[8], io[9]);
+    const float op = io[10];
 
     const float qn = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
     const float w = q4.x * qn, x = q4.y * qn, y = q4.z * qn, z = q4.w * qn;
@@ -475,7 +476,11 @@ __device__ __forceinline__ void project_backward_splat(const CamTable &cams, con
         dmean[1] += W[1] * dtx + W[4] * dty + W[7] * dtz;
         dmean[2] += W[2] * dtx + W[5] * dty + W[8] * dtz;
     }
-    if (!any) return;
+    if (!any) {
+#pragma unroll
+        for (int k = 0; k < kIO; ++k) io[k] = 0.f;
+        return;
+    }
 
     // Sigma = M M^T, M = R diag(s): dM = (dSig + dSig^T) M
     float ds[3] = {0.f, 0.f, 0.f}, dR[3][3];
@@ -499,21 +504,63 @@ __device__ __forceinline__ void project_backward_splat(const CamTable &cams, con
     const float dot = dqn[0] * w + dqn[1] * x + dqn[2] * y + dqn[3] * z;
     const float qv[4] = {w, x, y, z};
 #pragma unroll
-    for (int k = 0; k < 4; ++k) g_quats[4 * i + k] += (dqn[k] - qv[k] * dot) * qn;
+    for (int k = 0; k < 4; ++k) io[6 + k] = (dqn[k] - qv[k] * dot) * qn;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        g_means[3 * i + k] += dmean[k];
-        g_scales[3 * i + k] += ds[k];
+        io[k] = dmean[k];
+        io[3 + k] = ds[k];
     }
-    g_opac[i] += dop;
+    io[10] = dop;
 }
 
-// Splats per CTA of the per-splat pass. The CTA stages its splats' SH rows
-// in shared memory with coalesced loads (row stride 3K + 1 floats, odd, so a
-// warp reading one coefficient of 32 rows hits 32 banks) and accumulates the
-// SH gradients there ([coefficient][splat], stride kPB + 1), then adds them
-// to the caller's buffer with coalesced read-modify-writes.
+// Splats per CTA of the per-splat pass. The CTA stages its splats' inputs
+// and SH rows in shared memory with coalesced loads (row strides 11 and
+// 3K + 1 floats, odd, so a warp reading one value of 32 rows hits 32 banks),
+// accumulates the SH gradients there ([coefficient][splat], stride kPB + 1),
+// and adds all gradients to the caller's buffers with coalesced
+// read-modify-writes (none where a gradient is zero: splats no pixel saw).
 constexpr int kPB = 64;
+
+// Block-wide copy of n floats from global memory into shared memory
+// (put(idx, value)), U independent loads in flight per thread.
+template <int U, typename Put>
+__device__ __forceinline__ void stage_in(const float *__restrict__ src, int n, Put put)
+{
+    for (int base = threadIdx.x; base < n; base += kPB * U) {
+        float v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * kPB;
+            v[u] = idx < n ? __ldg(src + idx) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * kPB;
+            if (idx < n) put(idx, v[u]);
+        }
+    }
+}
+
+// Block-wide dst[idx] += get(idx) for idx < n, skipping zero addends (no
+// read or write for them), U independent loads in flight per thread.
+template <int U, typename Get>
+__device__ __forceinline__ void add_out(float *__restrict__ dst, int n, Get get)
+{
+    for (int base = threadIdx.x; base < n; base += kPB * U) {
+        float v[U], o[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * kPB;
+            v[u] = idx < n ? get(idx) : 0.f;
+            o[u] = v[u] != 0.f ? dst[idx] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * kPB;
+            if (v[u] != 0.f) dst[idx] = o[u] + v[u];
+        }
+    }
+}
 
 template <int D>
 __global__ void __launch_bounds__(kPB, 8)
@@ -529,28 +576,43 @@ project_backward_kernel(const __grid_constant__ CamTable cams, const __grid_cons
     constexpr int F = 3 * K, FS = F + 1, DS = kPB + 1;
     __shared__ float s_sh[kPB * FS];
     __shared__ float s_dsh[F * DS];
+    __shared__ float s_io[kPB * kIO];
     const int i0 = blockIdx.x * kPB;
     const int nb = min(kPB, P - i0);
-    {
-        const float *src = sh + (size_t)i0 * F;
-        for (int idx = threadIdx.x; idx < nb * F; idx += kPB) {
-            const int r = idx / F;
-            s_sh[r * FS + idx - r * F] = src[idx];
-        }
-        for (int k = threadIdx.x; k < F * DS; k += kPB) s_dsh[k] = 0.f;
+    // (source, floats per splat, first slot in the io row)
+    const float *src[4] = {means, scales, quats, opacities};
+    float *gdst[4] = {g_means, g_scales, g_quats, g_opac};
+    constexpr int kW[4] = {3, 3, 4, 1}, kOff[4] = {0, 3, 6, 10};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int wa = kW[a], oa = kOff[a];
+        stage_in<4>(src[a] + (size_t)i0 * wa, nb * wa, [&](int idx, float v) {
+            const int r = idx / wa;
+            s_io[r * kIO + oa + idx - r * wa] = v;
+        });
     }
+    stage_in<16>(sh + (size_t)i0 * F, nb * F, [&](int idx, float v) {
+        const int r = idx / F;
+        s_sh[r * FS + idx - r * F] = v;
+    });
+    for (int k = threadIdx.x; k < F * DS; k += kPB) s_dsh[k] = 0.f;
     __syncthreads();
     const int i = i0 + (int)threadIdx.x;
-    if (i < P) project_backward_splat<D>(cams, cfg, P, i, means, scales, quats, opacities,
-                                         s_sh + threadIdx.x * FS, s_dsh + threadIdx.x, DS, grad2d,
-                                         g_means, g_scales, g_quats, g_opac);
+    if (i < P) project_backward_splat<D>(cams, cfg, P, i, s_io + threadIdx.x * kIO, s_sh + threadIdx.x * FS,
+                                         s_dsh + threadIdx.x, DS, grad2d);
     __syncthreads();
-    float *dst = g_sh + (size_t)i0 * F;
-    for (int idx = threadIdx.x; idx < nb * F; idx += kPB) {
-        const int r = idx / F;
-        const float v = s_dsh[(idx - r * F) * DS + r];
-        if (v != 0.f) dst[idx] += v;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int wa = kW[a], oa = kOff[a];
+        add_out<4>(gdst[a] + (size_t)i0 * wa, nb * wa, [&](int idx) {
+            const int r = idx / wa;
+            return s_io[r * kIO + oa + idx - r * wa];
+        });
     }
+    add_out<12>(g_sh + (size_t)i0 * F, nb * F, [&](int idx) {
+        const int r = idx / F;
+        return s_dsh[(idx - r * F) * DS + r];
+    });
 }
 
 } // namespace
@@ -602,8 +664,9 @@ extern "C" gs_status gs_render_backward(void *stream, const gs_camera *cams, int
     const int ppt = (cfg->tile_w % 2 == 0) ? 2 : 1;
     if (cfg->tile_w * cfg->tile_h / ppt > 256) return GS_ERR_UNSUPPORTED;
     const int threads = cfg->tile_w * cfg->tile_h / ppt;
+    const size_t smem = bwd_smem_bytes(threads);
 #define GS_BWD_LAUNCH(K, PP)                                                                         \
-    blend_backward_kernel<K, PP><<<t.total_tiles, threads, 0, s>>>(t, c, rec, d_vals, rg, (uint32_t)N, \
+    blend_backward_kernel<K, PP><<<t.total_tiles, threads, smem, s>>>(t, c, rec, d_vals, rg, (uint32_t)N, \
                                                                    bg[0], bg[1], bg[2], d_final_T,   \
                                                                    d_last, d_grad_out, g2)
 #define GS_BWD_KIND(PP)                                                                              \

@@ -111,6 +111,8 @@ class Rasterizer:
             api.gs_workspace_status_async(self.workspace, self._status_dev[0:1])
             self._status_dev[1:4].copy_(self.count)
             self._status_host.copy_(self._status_dev, non_blocking=True)
+            if torch.cuda.is_current_stream_capturing():
+                return self.out  # a graph's replays are checked by their owner (autograd.GraphedStep)
             ev = torch.cuda.Event()
             ev.record()
             self._pending = ev
@@ -135,11 +137,12 @@ class Rasterizer:
             self._alloc(min(int(max(need, self.capacity) * 1.25) + 1024, MAX_CAPACITY))
         raise RuntimeError("overlap capacity could not be sized")
 
-    def check_deferred(self):
+    def check_deferred(self, event=None):
         """Waits for the last deferred pass's status copy (normally long
-        complete) and raises CapacityOverflow, after growing the buffers, if
-        that pass exceeded the overlap capacity."""
-        ev, self._pending = self._pending, None
+        complete; `event`: one recorded after it, e.g. after a graph replay)
+        and raises CapacityOverflow, after growing the buffers, if that pass
+        exceeded the overlap capacity."""
+        ev, self._pending = (event if event is not None else self._pending), None
         if ev is None:
             return
         ev.synchronize()

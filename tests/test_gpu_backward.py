@@ -170,6 +170,63 @@ def test_autograd_deferred_check_matches_synchronous(gs):
             assert torch.allclose(g[k], grads[0][k], rtol=1e-5, atol=1e-8), k
 
 
+def test_graphed_step_matches_eager_and_recaptures_on_overflow(gs):
+    """autograd.GraphedStep replays give the eager step's gradients; a
+    replay whose overlaps outgrow the buffers is reported by the next call
+    (CapacityOverflow, buffers grown, graph recaptured) and the repeated
+    step is right again."""
+    api, render, synth = gs
+    from paper_2603_18707_b300 import autograd
+    raw = _small_scene()
+    cam = synth.look_at([0.3, -0.2, -2.5], [0, 0, 0], 56, 48, 60.0)
+    probe = render.Rasterizer([cam], api.make_config("poly1", "opacity"), 48)
+    probe.forward(render.activate(raw))
+    need = probe.n_records()[1]
+    # an explicit capacity just above what the scene needs (kept, not shrunk)
+    R = render.Rasterizer([cam], api.make_config("poly1", "opacity"), 48, capacity=need + 8)
+    w = torch.randn(48 * 56, 3, device="cuda", generator=torch.Generator("cuda").manual_seed(2))
+    t = {k: torch.tensor(raw[k], device="cuda", requires_grad=True)
+         for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+
+    def fn():
+        for v in t.values():
+            v.grad = None
+        img = autograd.render(t["means"], t["log_scales"], t["quats"], t["opacity_logits"], t["sh"], 3, R,
+                              deferred=True)
+        loss = (img * w).sum()
+        loss.backward()
+        return loss
+
+    def eager():
+        R2 = render.Rasterizer([cam], api.make_config("poly1", "opacity"), 48)
+        t2 = {k: v.detach().clone().requires_grad_(True) for k, v in t.items()}
+        img = autograd.render(t2["means"], t2["log_scales"], t2["quats"], t2["opacity_logits"], t2["sh"], 3, R2)
+        (img * w).sum().backward()
+        return {k: v.grad for k, v in t2.items()}
+
+    def same(got, ref):
+        # the two runs differ only in the order of the FP32 atomic additions
+        for k in ref:
+            d = (got[k] - ref[k]).abs().max().item()
+            assert d <= 1e-4 * ref[k].abs().max().item(), (k, d)
+
+    G = autograd.GraphedStep(fn, R)
+    for _ in range(3):
+        G()
+    G.check()
+    same({k: v.grad for k, v in t.items()}, eager())
+    cap = R.capacity
+    with torch.no_grad():
+        t["log_scales"] += 1.5  # larger splats: many more overlaps than the buffers hold
+    G()
+    with pytest.raises(render.CapacityOverflow):
+        G()
+    assert R.overflows == 1 and R.capacity > cap
+    G()
+    G.check()
+    same({k: v.grad for k, v in t.items()}, eager())
+
+
 def test_differentiable_1M_scene_sampled_tiles(gs, orc):
     """1M-splat cluster scene at 1024x1024: L1 loss against the render of a
     perturbed copy. The full gradient is finite; with the loss restricted to
