@@ -58,6 +58,9 @@ constexpr int kSpinLimit = 1 << 20;
 #else
 #define GS_EMIT_BOUNDS __launch_bounds__(256)
 #endif
+#ifndef GS_EMIT_RUNS
+#define GS_EMIT_RUNS 1 // tile-digit histogram adds of the higher digits per run of equal digits
+#endif
 #ifndef GS_EMIT_ITEMS
 #define GS_EMIT_ITEMS 8
 #endif
@@ -555,8 +558,13 @@ emit_kernel(const __grid_constant__ CamTable cams, FastDiv pdiv, uint32_t n_reco
         const bool valid = idx < nv && vv < n_records; // ids are < n_records unless a wait timed out
         if (!valid) vv = 0u;
         v[j] = vv;
-        cnt[j] = valid ? tiles[vv] : 0u;
         rc[j] = valid ? rects[vv] : make_ushort4(0, 0, 0, 0);
+        // a drawn record's rectangle holds exactly its tiles unless rows are
+        // cut to the ellipse: one gather per record instead of two
+        if (ELL)
+            cnt[j] = valid ? tiles[vv] : 0u;
+        else
+            cnt[j] = valid ? ((uint32_t)rc[j].z - rc[j].x + 1u) * ((uint32_t)rc[j].w - rc[j].y + 1u) : 0u;
         const uint32_t x = warp_incl_scan(cnt[j]);
         incl[j] = x;
         off[j] = running;
@@ -676,13 +684,33 @@ emit_kernel(const __grid_constant__ CamTable cams, FastDiv pdiv, uint32_t n_reco
             row += ((row + 1u) * erw <= l) ? 1u : 0u;
             const uint32_t col = l - row * erw;
             const uint32_t o = out_base + p;
-            if (p < w_total && o < capacity) {
-                const uint32_t key = etb + row * etx + col;
+            const bool act = p < w_total && o < capacity; // a prefix of the warp's lanes
+            const uint32_t key = etb + row * etx + col;
+            if (act) {
                 keys_out[o] = key;
                 vals_out[o] = ev;
-                for (int q = 0; q < plan.passes; ++q)
-                    atomicAdd(&s_h[q][(key >> plan.shift[q]) & ((1u << plan.bits[q]) - 1u)], 1u);
+                atomicAdd(&s_h[0][(key >> plan.shift[0]) & ((1u << plan.bits[0]) - 1u)], 1u);
             }
+#if GS_EMIT_RUNS
+            // higher digits: consecutive lanes mostly hold consecutive tile
+            // ids with one digit; one atomic per run of equal digits
+            const uint32_t nact = __popc(__ballot_sync(0xffffffffu, act));
+            for (int q = 1; q < plan.passes; ++q) {
+                const uint32_t d = (key >> plan.shift[q]) & ((1u << plan.bits[q]) - 1u);
+                const uint32_t dp = __shfl_up_sync(0xffffffffu, d, 1);
+                const bool head = act && (lane == 0 || dp != d);
+                const uint32_t heads = __ballot_sync(0xffffffffu, head);
+                if (head) {
+                    const uint32_t after = heads & (0xfffffffeu << lane);
+                    const uint32_t next = after ? (uint32_t)(__ffs(after) - 1) : 32u;
+                    atomicAdd(&s_h[q][d], min(next, nact) - (uint32_t)lane);
+                }
+            }
+#else
+            if (act)
+                for (int q = 1; q < plan.passes; ++q)
+                    atomicAdd(&s_h[q][(key >> plan.shift[q]) & ((1u << plan.bits[q]) - 1u)], 1u);
+#endif
         }
     }
     if (part == nparts - 1 && threadIdx.x == 0) {
