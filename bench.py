@@ -127,6 +127,8 @@ def parse():
     p.add_argument("--tile", type=str, default=None, help="tile shape WxH, e.g. 16x16")
     p.add_argument("--rect", choices=["aabb", "circle", "ellipse"], default=None,
                    help="tile binning around the support ellipse")
+    p.add_argument("--leg", choices=list(LEGS), default=None,
+                   help="run only this extra leg and print its result (profiling; no headline line)")
     p.add_argument("--profile", choices=["poly1", "exp", "poly2", "poly3"], default=None,
                    help="run only `steps` passes of one arm (for ncu), print no bench line")
     return p.parse_args()
@@ -704,10 +706,21 @@ def bench_batched(a):
     return out
 
 
+LEGS = {}
+
+
 def main():
     a = parse()
     world, rank, local = dist_setup(a)
-    if a.impl == "reference":
+    if a.leg:
+        import torch
+        from paper_2603_18707_b300 import build as _build
+        torch.cuda.set_device(local)
+        _build.build()
+        res = LEGS[a.leg](a)
+        if rank == 0:
+            print(json.dumps({"leg": a.leg, "steps": a.steps, **res}), flush=True)
+    elif a.impl == "reference":
         run_reference(a, world, rank)
     else:
         run_ours(a, world, rank, local)
@@ -715,6 +728,9 @@ def main():
         import torch.distributed as dist
         dist.destroy_process_group()
 
+
+LEGS.update(differentiable=bench_differentiable, batched=bench_batched, fp16x2=bench_fp16x2,
+            f2_range=bench_f2_range, tensor_quadric=bench_tensor_quadric)
 
 if __name__ == "__main__":
     main()
