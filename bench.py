@@ -77,6 +77,14 @@ def binsort_bytes(r) -> dict:
     return {"ours": ours, "3dgs_design": ref}
 
 
+# Pipe utilisation of the same blend kernel from its full-section ncu capture
+# (1M splats, 4 cameras at 1920x1080; the kernel's code, not the scene, sets
+# these): the FMA-pipe fraction the metric asks for, beside the FLOP-based
+# roofline fraction. Reset with BLEND_TRAFFIC when the blend changes.
+BLEND_NCU = {"issue_active": 0.783, "fma_pipe": 0.335, "alu_pipe": 0.478, "lanes_active_of_32": 15.9,
+             "source": "ncu --set full, render_kernel<POLY1, 4, FP32>, 1M splats x 4 cameras"}
+
+
 def _default_workload(a) -> bool:
     """The configuration BLEND_TRAFFIC was captured on."""
     return ((a.splats, a.cams, a.width, a.height) == (3_000_000, 16, 1920, 1080)
@@ -450,6 +458,7 @@ def run_ours(a, world, rank, local):
     roofline = {"bound": "alu", "kernel": "blend (render_kernel<POLY1>)", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": BLEND_TRAFFIC if _default_workload(a) else None,
+                "ncu_pipes": BLEND_NCU if _default_workload(a) else None,
                 "peak_source": "measured FFMA rate (gs_fma_peak, this run); derived "
                                f"148 SMs x 128 lanes x 2 FLOP x 2032 MHz = {peak_derived:.1f}",
                 "dominant_stage": dom}

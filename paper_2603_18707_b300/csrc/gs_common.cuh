@@ -219,8 +219,9 @@ __device__ __forceinline__ bool row_cols(float mx, float my, float A, float B, f
     const float xmin = (-dys >= dya && -dys <= dyb) ? mx - hx : mx + fminf(ca - wa, cb - wb);
     const float p0 = fmaxf(ceilf(xmin - 0.5f), 0.f), p1 = fminf(floorf(xmax - 0.5f), (float)(W - 1));
     if (!(p0 <= p1)) return false;
-    c0 = max((int)p0 / tile_w, cx0);
-    c1 = min((int)p1 / tile_w, cx1);
+    // p0, p1 >= 0 and tile sizes are powers of two: a shift divides
+    c0 = max((int)p0 >> (__ffs(tile_w) - 1), cx0);
+    c1 = min((int)p1 >> (__ffs(tile_w) - 1), cx1);
     return c0 <= c1;
 }
 

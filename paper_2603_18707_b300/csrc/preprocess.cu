@@ -137,6 +137,7 @@ preprocess_kernel(const __grid_constant__ CamTable cams, const __grid_constant__
     const float S12 = M10 * M20 + M11 * M21 + M12 * M22;
     const float S22 = M20 * M20 + M21 * M21 + M22 * M22;
 
+    const int sw = __ffs(cfg.tile_w) - 1, shh = __ffs(cfg.tile_h) - 1; // log2 of the tile size
     for (int c = 0; c < cams.ncam; ++c) {
         const CamDev &cm = cams.cam[c];
         const int64_t n = (int64_t)c * P + i;
@@ -172,9 +173,9 @@ preprocess_kernel(const __grid_constant__ CamTable cams, const __grid_constant__
             const float det1 = a * cc - b * b;
             drawn = det1 > 0.f;
             if (drawn) {
-                const float rho = cfg.aa ? sqrtf(fmaxf(det0, 0.f) / det1) : 1.f;
-                const float o2 = op * rho;
                 const float idet = 1.f / det1;
+                const float rho = cfg.aa ? sqrtf(fmaxf(det0, 0.f) * idet) : 1.f;
+                const float o2 = op * rho;
                 const float mx2 = cm.fx * tx * iz + cm.cx;
                 const float my2 = cm.fy * ty * iz + cm.cy;
                 float xc = support_threshold(cfg, o2);
@@ -198,8 +199,9 @@ preprocess_kernel(const __grid_constant__ CamTable cams, const __grid_constant__
                     r0 = make_float4(mx2, my2, o2, tz);
                     r1 = make_float4(cc * idet, -b * idet, a * idet, xc);
                     if (px0 <= px1 && py0 <= py1) {
-                        const int gx0 = (int)px0 / cfg.tile_w, gx1 = (int)px1 / cfg.tile_w;
-                        const int gy0 = (int)py0 / cfg.tile_h, gy1 = (int)py1 / cfg.tile_h;
+                        // pixel -> tile: non-negative, power-of-two tile sizes
+                        const int gx0 = (int)px0 >> sw, gx1 = (int)px1 >> sw;
+                        const int gy0 = (int)py0 >> shh, gy1 = (int)py1 >> shh;
                         rect = make_ushort4(gx0, gy0, gx1, gy1);
                         if (cfg.rect_mode == GS_RECT_ELLIPSE && gx1 > gx0 && gy1 > gy0) {
                             // only the tiles of each row that the ellipse reaches (a
