@@ -79,6 +79,16 @@ class Rasterizer:
         self.keys64 = (torch.empty(max(self.capacity, 1), dtype=torch.int64, device=self.device)
                        if self.keep_keys else None)
 
+    def set_cameras(self, cams):
+        """New poses (and intrinsics) for the same number of cameras at the
+        same resolutions: the buffers stay valid. Cameras reach the kernels
+        as launch parameters, so this costs no device copy."""
+        arr = api.camera_array(cams)
+        if len(arr) != self.ncam or any((a.width, a.height) != (b.width, b.height)
+                                        for a, b in zip(arr, self.cams)):
+            raise ValueError("set_cameras keeps the camera count and resolutions")
+        self.cams = arr
+
     def preprocess(self, sc: dict):
         api.gs_preprocess(self.cams, self.P, sc["means"], sc["scales"], sc["quats"],
                           sc["opacities"], sc["sh"], sc["sh_degree"], self.cfg, self.splat2d)
@@ -231,6 +241,15 @@ class StreamedRasterizer:
             self.parts.append(Rasterizer(cs, cfg, P, device=device, keep_keys=keep_keys, outputs=views))
             o += n
         self.streams = [torch.cuda.Stream(device=self.device) for _ in self.parts]
+        self.bounds = bounds
+
+    def set_cameras(self, cams):
+        cams = list(cams)
+        if len(cams) != self.ncam:
+            raise ValueError("set_cameras keeps the camera count and resolutions")
+        for k, r in enumerate(self.parts):
+            r.set_cameras(cams[self.bounds[k]:self.bounds[k + 1]])
+        self.cams = api.camera_array(cams)
 
     def preprocess(self, sc: dict):
         for r in self.parts:
@@ -332,6 +351,23 @@ class HostPipeline:
         self.R.run_async(self.dev_in[b])
         self.dev_out[b].copy_(self.R.out, non_blocking=True)
         self.ev_in_free[b].record(cur)
+        self.ev_rendered[b].record(cur)
+        self.d2h.wait_event(self.ev_rendered[b])
+        with torch.cuda.stream(self.d2h):
+            host_out.copy_(self.dev_out[b], non_blocking=True)
+            self.ev_out_free[b].record(self.d2h)
+
+    def step_views(self, sc: dict, cams, host_out: torch.Tensor):
+        """Enqueues one frame of a resident scene (serving): new camera
+        poses (launch parameters, no copy) -> host_out (pinned). Step k's
+        download runs on the copy stream while step k + 1 renders."""
+        b = self.k & 1
+        self.k += 1
+        cur = torch.cuda.current_stream(self.R.out.device)
+        cur.wait_event(self.ev_out_free[b])  # the download of this image buffer is done
+        self.R.set_cameras(cams)
+        self.R.run_async(sc)
+        self.dev_out[b].copy_(self.R.out, non_blocking=True)
         self.ev_rendered[b].record(cur)
         self.d2h.wait_event(self.ev_rendered[b])
         with torch.cuda.stream(self.d2h):

@@ -189,3 +189,32 @@ def test_host_pipeline_frames_match_device_renders():
     torch.cuda.synchronize()
     for k in range(5):
         assert torch.equal(outs[k], want[k % 2].cpu()), k
+
+
+def test_set_cameras_and_serving_pipeline(gs):
+    """New poses on an existing (streamed) rasterizer render exactly what a
+    fresh rasterizer renders for them; HostPipeline.step_views delivers the
+    same images to pinned host memory."""
+    from paper_2603_18707_b300 import api, render, synth
+    raw = synth.scene_clusters(200_000, 0, sh_degree=3)
+    sc = render.activate(raw)
+    cfg = api.make_config("poly1", "opacity")
+    a = synth.orbit_cameras(4, 320, 240)
+    b = synth.orbit_cameras(4, 320, 240, phase=0.3)
+    R = render.StreamedRasterizer(a, cfg, 200_000, groups=2)
+    R.forward(sc)
+    R.set_cameras(b)
+    R.forward(sc)
+    ref = render.Rasterizer(b, cfg, 200_000)
+    ref.forward(sc)
+    torch.cuda.synchronize()
+    assert torch.equal(R.out, ref.out)
+    with pytest.raises(ValueError):
+        R.set_cameras(synth.orbit_cameras(4, 321, 240))
+    host = torch.empty_like(R.out, device="cpu").pin_memory()
+    pipe = render.HostPipeline(R)
+    pipe.step_views(sc, a, host)
+    pipe.step_views(sc, b, host)
+    pipe.finish()
+    torch.cuda.synchronize()
+    assert torch.equal(host, ref.out.cpu())
