@@ -19,7 +19,7 @@ namespace gs {
 
 struct BlendCoef {
     float4 a; // ux, uy, u0, vy
-    float4 b; // v0, p0, p1, p2
+    float4 b; // v0, p0, p1, p2 (f1, exp: x_cut)
     float4 c; // red, green, blue, p3
 };
 
@@ -46,6 +46,12 @@ __device__ __forceinline__ BlendCoef make_coef(const CfgDev &cfg, float4 r0, flo
         p2 = o * cfg.c[2];
         p3 = o * cfg.c[3];
     }
+    // f1 and exp evaluate alpha from p0, p1 alone; their p2 slot carries
+    // the record's cut x_cut instead (Eq. 3-5, with the preprocessing's
+    // margin): where a lower bound of Q exceeds it, no pixel reaches eps.
+    // The legacy 3-sigma cut does not bound the eps support, so it never
+    // skips.
+    if (KIND == GS_K_POLY1 || KIND == GS_K_EXP) p2 = (cfg.cull == GS_CULL_LEGACY3) ? INFINITY : r1.w;
     k.b = make_float4(-vy * my, p0, p1, p2);
     k.c = make_float4(r2.x, r2.y, r2.z, p3);
     return k;

@@ -179,7 +179,11 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                 const float ua = fmaf(a.x, xs[0], ub), uz = fmaf(a.x, xs[PPT - 1], ub);
                 const float um = ((ua > 0.f) != (uz > 0.f)) ? 0.f : fminf(fabsf(ua), fabsf(uz));
 #endif
-                if (alpha_of_q<KIND>(cfg, b, p3, fmaf(um, um, v2)) < eps_skip) continue;
+                if constexpr (!HALF && (KIND == GS_K_POLY1 || KIND == GS_K_EXP)) {
+                    if (fmaf(um, um, v2) > b.w) continue; // beyond the record's cut x_cut
+                } else {
+                    if (alpha_of_q<KIND>(cfg, b, p3, fmaf(um, um, v2)) < eps_skip) continue;
+                }
             }
             float al[PPT];
             if (HALF) {
