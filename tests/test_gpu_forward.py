@@ -78,6 +78,36 @@ def test_preprocess_parity(gs, orc, small):
         assert (rg != ro).any(axis=1).sum() <= max(3, both.sum() // 200)
 
 
+@pytest.mark.parametrize("kind,cull", [("exp", "opacity"), ("poly1", "opacity"), ("poly1", "universal"),
+                                       ("poly3", "opacity")])
+def test_border_splats_never_dropped(gs, orc, kind, cull):
+    """Large anisotropic splats scattered around the image border (most
+    projected outside it, many reaching in): every record the FP64 oracle
+    draws is drawn on the GPU, with a rectangle containing the oracle's
+    (the FP32 support and rectangle are conservative)."""
+    from paper_2603_18707_b300 import synth
+    r = np.random.default_rng(11)
+    P = 3000
+    raw = synth.scene_uniform(P, 5)
+    raw["means"] = np.stack([r.uniform(-2.8, 2.8, P), r.uniform(-2.8, 2.8, P), r.uniform(-0.6, 0.6, P)],
+                            1).astype(np.float32)
+    raw["log_scales"] = np.stack([r.normal(-2.4, 0.6, P), r.normal(-3.5, 0.6, P), r.normal(-3.0, 0.6, P)],
+                                 1).astype(np.float32)
+    raw["opacity_logits"] = r.normal(1.0, 2.0, P).astype(np.float32)
+    cam = synth.camera_small()
+    R = _gpu(gs, raw, [cam], kind, cull)
+    g = parse_splat2d(R.splat2d.cpu().numpy(), R.P)
+    o = orc.splats_to_numpy(orc.project(orc.activate(raw), orc.camera_from_dict(cam),
+                                        _oracle_cfg(orc, kind, cull)), R.P)
+    vis_g = g["tiles"] > 0
+    vis_o = (o["visible"] == 1) & (o["tiles"] > 0)
+    assert vis_o.sum() > 500 and (~vis_o).sum() > 500  # both sides of the border are exercised
+    assert not (vis_o & ~vis_g).any()
+    both = vis_g & vis_o
+    ro, rg = o["rect"][both], g["rect"][both]
+    assert np.all(rg[:, :2] <= ro[:, :2]) and np.all(rg[:, 2:] >= ro[:, 2:])
+
+
 @pytest.mark.parametrize("case", ["small3cam", "clusters", "ties"])
 def test_binning_bit_exact(gs, case):
     """Sorted record ids, 64-bit (tile, depth) keys and per-tile ranges equal a
