@@ -86,6 +86,25 @@ BLEND_NCU = {"issue_active": 0.783, "fma_pipe": 0.342, "alu_pipe": 0.466, "lanes
              "source": "ncu --set full, render_kernel<POLY1, 4, FP32>, 1M splats x 4 cameras"}
 
 
+def load_scene(a, P: int, seed: int = 0):
+    """The cluster scene (SH degree 3), activated on the GPU and, unless
+    --splat-order input, stored in Z-order of the means (render.spatial_order,
+    a one-time preparation at load, timed with CUDA events). Returns (raw
+    numpy scene, activated scene, permutation or None, ms of the reorder)."""
+    import torch
+    from paper_2603_18707_b300 import render, synth
+    raw = synth.scene_clusters(P, seed, sh_degree=3)
+    sc = render.activate(raw)
+    if getattr(a, "splat_order", "zorder") == "input":
+        return raw, sc, None, 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    sc, perm = render.spatial_order(sc)
+    e1.record()
+    torch.cuda.synchronize()
+    return raw, sc, perm, e0.elapsed_time(e1)
+
+
 def _default_workload(a) -> bool:
     """The configuration BLEND_TRAFFIC was captured on."""
     return ((a.splats, a.cams, a.width, a.height) == (3_000_000, 16, 1920, 1080)
@@ -128,6 +147,9 @@ def parse():
     p.add_argument("--no-fp16", action="store_true", help="skip the FP16x2 precision leg")
     p.add_argument("--no-f2range", action="store_true", help="skip the range-extended f2 leg")
     p.add_argument("--no-tensor", action="store_true", help="skip the tensor-core quadric leg")
+    p.add_argument("--splat-order", choices=["zorder", "input"], default="zorder",
+                   help="store the scene in Z-order of the means once at load (default) or keep "
+                        "the generator's order")
     p.add_argument("--upload-streams", type=int, default=1,
                    help="copy streams the end-to-end leg splits each step's upload over")
     p.add_argument("--groups", type=int, default=2,
@@ -150,6 +172,8 @@ def workload(a):
             "sh_degree": 3, "tile": "16x16", "kernel": "poly1", "cull": "opacity",
             "baseline_kernel": "exp", "baseline_cull": "opacity",
             "camera_sets_on_streams": getattr(a, "groups", 1),
+            "splat_order": ("z-order of the means, stored once at load (render.spatial_order)"
+                            if getattr(a, "splat_order", "zorder") == "zorder" else "generator order"),
             "l2": "inputs larger than L2 (scene 0.7 GB, records 3 GB per step)"}
 
 
@@ -314,11 +338,10 @@ def run_ours(a, world, rank, local):
 
     torch.cuda.set_device(local)
     _build.build()
-    raw = synth.scene_clusters(a.splats, 0, sh_degree=3)
+    raw, sc, _, order_ms = load_scene(a, a.splats)
     # each rank renders a.cams views of its own (interleaved on one orbit):
     # the cameras are the units sharded across ranks, with no exchange
     cams = synth.shard_orbit(a.cams, rank, world, a.width, a.height)
-    sc = render.activate(raw)
     P = a.splats
     over = {}
     if a.ppt:
@@ -521,7 +544,8 @@ def run_ours(a, world, rank, local):
     fps = world * a.cams / (ms / 1e3)
     line = {"metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload(a),
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload(a), splat_order_ms_once=order_ms),
             "gsplat_evals_per_s": evals_all["poly1"] / (ms / 1e3) / 1e9,
             "exp": {"frames_per_s": world * a.cams / (res["exp"] / 1e3), "ms_per_step": res["exp"],
                     "gsplat_evals_per_s": evals_all["exp"] / (res["exp"] / 1e3) / 1e9},
@@ -555,14 +579,20 @@ def bench_differentiable(a):
 
     from paper_2603_18707_b300 import api, autograd, render, synth
     P = 1_000_000
+    keys = ("means", "log_scales", "quats", "opacity_logits", "sh")
     raw = synth.scene_clusters(P, 0, sh_degree=3)
+    tgt = synth.perturbed(raw, 1)
+    if getattr(a, "splat_order", "zorder") == "zorder":
+        # parameters and target stored in the Z-order of the parameters' means, once
+        raw, perm = render.spatial_order(raw, keys)
+        tgt = {k: (api.gs_gather_rows(torch.as_tensor(v, device="cuda").contiguous(), perm) if k in keys else v)
+               for k, v in tgt.items()}
     cam = synth.orbit_cameras(1, 1024, 1024)[0]
     cfg = api.make_config("poly1", "opacity")
     Rt = render.Rasterizer([cam], cfg, P)
-    target = Rt.forward(render.activate(synth.perturbed(raw, 1))).clone()
+    target = Rt.forward(render.activate(tgt)).clone()
     del Rt
-    t = {k: torch.tensor(raw[k], device="cuda", requires_grad=True)
-         for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+    t = {k: torch.as_tensor(raw[k], device="cuda").clone().requires_grad_(True) for k in keys}
     R = render.Rasterizer([cam], cfg, P)
 
     def step(deferred):
@@ -618,9 +648,8 @@ def bench_fp16x2(a):
     import torch
 
     from paper_2603_18707_b300 import api, render, synth
-    raw = synth.scene_clusters(a.splats, 0, sh_degree=3)
+    raw, sc, _, _ = load_scene(a, a.splats)
     cams = synth.orbit_cameras(a.cams, a.width, a.height)
-    sc = render.activate(raw)
     out = {}
     for kind in ("poly1", "poly2"):
         res = {}
@@ -654,9 +683,8 @@ def bench_f2_range(a):
     import numpy as np
 
     from paper_2603_18707_b300 import api, render, synth
-    raw = synth.scene_clusters(a.splats, 0, sh_degree=3)
+    raw, sc, _, _ = load_scene(a, a.splats)
     cams = synth.orbit_cameras(a.cams, a.width, a.height)
-    sc = render.activate(raw)
     ref = {}
     for kind in ("exp", "poly1"):
         R = render.Rasterizer(cams, api.make_config(kind, "opacity"), a.splats)
@@ -685,9 +713,8 @@ def bench_tensor_quadric(a):
     split weights (config tensor_alpha), against the FP32 blend: frames/s
     and the largest per-channel difference of the images."""
     from paper_2603_18707_b300 import api, render, synth
-    raw = synth.scene_clusters(a.splats, 0, sh_degree=3)
+    raw, sc, _, _ = load_scene(a, a.splats)
     cams = synth.orbit_cameras(a.cams, a.width, a.height)
-    sc = render.activate(raw)
     out = {}
     for kind in ("poly1", "exp"):
         res, imgs, blend = {}, {}, {}
@@ -716,9 +743,8 @@ def bench_batched(a):
 
     from paper_2603_18707_b300 import api, autotune, render, synth
     P = 6_000_000
-    raw = synth.scene_clusters(P, 0, sh_degree=3)
+    raw, sc, _, _ = load_scene(a, P)
     cams = synth.mixed_cameras(64)
-    sc = render.activate(raw)
     npix = sum(c["width"] * c["height"] for c in cams)
     out = {"workload": "6M-splat cluster scene, SH degree 3, 64 cameras 4:3:2:1 of "
                        "640x360/1280x720/1920x1080/3840x2160", "megapixels": npix / 1e6}

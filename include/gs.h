@@ -11,6 +11,8 @@
  *                       overlap emission, per-tile ranges
  *   gs_render           front-to-back alpha blending per tile (Sec. 2, Eq. 1/2/6)
  *   gs_render_backward  reverse blend + chain rule to the splat inputs (Sec. 4.3)
+ * Scene preparation (once per scene, not per frame):
+ *   gs_spatial_order    Z-order permutation of the splats; gs_gather_rows applies it
  *
  * Conventions shared by every entry point:
  *  - Pointers named d_* are DEVICE pointers; everything else is host memory.
@@ -295,6 +297,31 @@ uint64_t gs_launch_count(void);
 
 /* Human-readable name of a status bit. */
 const char *gs_status_string(int32_t status);
+
+/* Spatial order of a scene (a one-time preparation when a scene is loaded,
+ * not part of a frame; the paper has no counterpart). d_perm[k] is the index
+ * of the k-th splat along a Z-order (Morton) curve: each mean's coordinates
+ * are scaled into 10 bits over the bounding box of the finite means and
+ * interleaved (x in bit 0); equal codes keep ascending index order; a
+ * non-finite coordinate counts as the box's lower end. Storing the splats in
+ * this order (gs_gather_rows) lets warps of nearby splats project, cull and
+ * gather records together; rendered images change only where two splats
+ * share a tile at exactly equal depth (their order follows the index).
+ * d_means [P][3] FP32 (device); d_perm [P] uint32 (device, written);
+ * d_workspace: gs_spatial_order_workspace_bytes(P) bytes of device memory,
+ * 256-byte aligned, owned by the caller (contents need no initialisation).
+ * Stream-ordered. GS_ERR_ARG for P < 0, P >= 2^30 or a null / misaligned
+ * pointer with P > 0; P = 0 does nothing. */
+size_t gs_spatial_order_workspace_bytes(int32_t P);
+gs_status gs_spatial_order(void *stream, int32_t P, const float *d_means, void *d_workspace,
+                           uint32_t *d_perm);
+
+/* Row gather for reordering a scene: dst row k = src row perm[k], for n rows
+ * of row_bytes bytes each (a positive multiple of 4; src, dst 4-byte
+ * aligned, not overlapping). A perm entry >= n writes a zero row.
+ * Stream-ordered; GS_ERR_ARG for a bad size or pointer. */
+gs_status gs_gather_rows(void *stream, int32_t n, int32_t row_bytes, const void *d_src,
+                         const uint32_t *d_perm, void *d_dst);
 
 #ifdef __cplusplus
 }

@@ -178,6 +178,30 @@ def gs_workspace_status_async(workspace, dst, stream=None) -> None:
                                                                        _p(dst)))
 
 
+def gs_spatial_order(means, stream=None):
+    """Z-order permutation of the splats (int32 tensor [P]; see gs.h):
+    store a scene in this order once when it is loaded."""
+    P = int(means.shape[0])
+    perm = torch.empty(max(P, 1), dtype=torch.int32, device=means.device)
+    if P:
+        ws = torch.empty(lib().gs_spatial_order_workspace_bytes(P), dtype=torch.uint8, device=means.device)
+        check("gs_spatial_order", lib().gs_spatial_order(_stream(stream), P, _f32(means), _p(ws), _p(perm)))
+    return perm[:P]
+
+
+def gs_gather_rows(src, perm, dst=None, stream=None):
+    """dst[k] = src[perm[k]] row-wise (any 4-byte dtype layout; rows are the
+    first dimension)."""
+    n = int(perm.shape[0])
+    if dst is None:
+        dst = torch.empty((n,) + tuple(src.shape[1:]), dtype=src.dtype, device=src.device)
+    row = src[0].numel() * src.element_size() if src.shape[0] else 4
+    if dst.shape[1:] != src.shape[1:] or dst.dtype != src.dtype or dst.shape[0] != n:
+        raise ValueError("dst must have perm's length and src's row shape and dtype")
+    check("gs_gather_rows", lib().gs_gather_rows(_stream(stream), n, int(row), _p(src), _p(perm), _p(dst)))
+    return dst
+
+
 def gs_selftest_lookback_timeout(which: int, scratch, spin_limit: int, stream=None) -> None:
     """Runs a look-back against a predecessor that never publishes (which 0:
     scalar, 1: per digit); the error word scratch[0] then holds

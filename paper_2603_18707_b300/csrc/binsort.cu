@@ -997,3 +997,201 @@ extern "C" gs_status gs_selftest_lookback_timeout(void *stream, int32_t which, u
     }
     return GS_OK;
 }
+
+// ---- spatial order of a scene (one-time preparation) ---------------------
+// Bounding box of the finite means (order-preserving integer images of the
+// floats, so that atomicMin / atomicMax compare them), 30-bit Morton codes
+// with the four 8-bit digit histograms, then four Onesweep passes of
+// (code, index): a stable sort, ties in index order.
+namespace gs {
+namespace {
+
+struct OrderWs {
+    size_t hdr, box, hist, st, k0, k1, v1, total;
+    uint32_t parts;
+    size_t st_stride;
+};
+
+OrderWs order_layout(int64_t P)
+{
+    OrderWs L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o += align256(bytes); return r; };
+    L.parts = (uint32_t)((P + kSortTile - 1) / kSortTile);
+    L.st_stride = (size_t)256 * (L.parts + 1);
+    L.hdr = take(sizeof(WsHeader));
+    L.box = take(sizeof(uint32_t) * 6);
+    L.hist = take(sizeof(uint32_t) * 4 * kHistSlot);
+    L.st = take(sizeof(uint32_t) * 4 * L.st_stride);
+    L.k0 = take(sizeof(uint32_t) * P + 16);
+    L.k1 = take(sizeof(uint32_t) * P + 16);
+    L.v1 = take(sizeof(uint32_t) * P + 16);
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ uint32_t ford(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float funord(uint32_t u)
+{
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// box[0..2] = images of the minima (start at all ones), box[3..5] = of the
+// maxima (start at zero); also publishes the element count for the sorts.
+__global__ void __launch_bounds__(256) bbox_kernel(const float *__restrict__ means, int P, uint32_t *box,
+                                                   WsHeader *hdr)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) hdr->n_vis = (uint32_t)P;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float v = means[3 * (size_t)i + k];
+            if (isfinite(v)) {
+                lo[k] = fminf(lo[k], v);
+                hi[k] = fmaxf(hi[k], v);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        uint32_t a = ford(lo[k]), b = ford(hi[k]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a = min(a, __shfl_xor_sync(0xffffffffu, a, o));
+            b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&box[k], a);
+            atomicMax(&box[3 + k], b);
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t spread10(uint32_t x)
+{
+    x &= 0x3ffu;
+    x = (x | (x << 16)) & 0x030000FFu;
+    x = (x | (x << 8)) & 0x0300F00Fu;
+    x = (x | (x << 4)) & 0x030C30C3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+__global__ void __launch_bounds__(256) morton_kernel(const float *__restrict__ means, int P,
+                                                     const uint32_t *box, uint32_t *__restrict__ keys,
+                                                     uint32_t *__restrict__ vals, uint32_t *hist)
+{
+    __shared__ uint32_t s_h[4][256];
+    for (int i = threadIdx.x; i < 4 * 256; i += 256) (&s_h[0][0])[i] = 0;
+    __syncthreads();
+    float lo[3], sc[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = funord(box[k]);
+        const float ext = funord(box[3 + k]) - lo[k];
+        // no finite mean (ext = -inf) or a flat box: every code is 0 on that axis
+        sc[k] = (ext > 0.f && isfinite(ext)) ? 1023.f / ext : 0.f;
+        if (!isfinite(lo[k])) lo[k] = 0.f;
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
+        uint32_t code = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            // fmaxf / fminf drop a NaN operand: a non-finite coordinate maps to 0 or 1023
+            const float q = fminf(fmaxf((means[3 * (size_t)i + k] - lo[k]) * sc[k], 0.f), 1023.f);
+            code |= spread10((uint32_t)q) << k;
+        }
+        keys[i] = code;
+        vals[i] = (uint32_t)i;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) atomicAdd(&s_h[p][(code >> (8 * p)) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * 256; i += 256) {
+        const uint32_t v = (&s_h[0][0])[i];
+        if (v) atomicAdd(&hist[(i >> 8) * kHistSlot + (i & 255)], v);
+    }
+}
+
+__global__ void __launch_bounds__(256) gather_rows_kernel(int64_t total, int words,
+                                                          const uint32_t *__restrict__ src,
+                                                          const uint32_t *__restrict__ perm, int n,
+                                                          uint32_t *__restrict__ dst)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = e / words, w = e - k * words;
+        const uint32_t p = perm[k];
+        dst[e] = p < (uint32_t)n ? src[(int64_t)p * words + w] : 0u;
+    }
+}
+
+} // namespace
+} // namespace gs
+
+extern "C" size_t gs_spatial_order_workspace_bytes(int32_t P)
+{
+    if (P < 0 || P >= (int32_t)kValMask) return 0;
+    return order_layout(P).total;
+}
+
+extern "C" gs_status gs_spatial_order(void *stream, int32_t P, const float *d_means, void *d_workspace,
+                                      uint32_t *d_perm)
+{
+    if (P < 0 || P >= (int32_t)kValMask) return GS_ERR_ARG;
+    if (P == 0) return GS_OK;
+    if (!d_means || !d_workspace || !d_perm || ((uintptr_t)d_workspace & 255) || ((uintptr_t)d_means & 3) ||
+        ((uintptr_t)d_perm & 3))
+        return GS_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const OrderWs L = order_layout(P);
+    char *ws = static_cast<char *>(d_workspace);
+    auto U = [&](size_t off) { return reinterpret_cast<uint32_t *>(ws + off); };
+    WsHeader *hdr = reinterpret_cast<WsHeader *>(ws + L.hdr);
+    // zero the header, histograms and look-back states; the box's minima start at all ones
+    if (cudaMemsetAsync(ws, 0, L.k0, s) != cudaSuccess) return GS_ERR_CUDA;
+    if (cudaMemsetAsync(U(L.box), 0xff, sizeof(uint32_t) * 3, s) != cudaSuccess) return GS_ERR_CUDA;
+    const unsigned blocks = (unsigned)std::min<int64_t>((P + 255) / 256, 148 * 8);
+    bbox_kernel<<<blocks, 256, 0, s>>>(d_means, P, U(L.box), hdr);
+    count_launch();
+    GS_LAUNCH_CHECK();
+    // (code, index) into (k0, d_perm); the passes ping-pong back into them
+    morton_kernel<<<blocks, 256, 0, s>>>(d_means, P, U(L.box), U(L.k0), d_perm, U(L.hist));
+    count_launch();
+    GS_LAUNCH_CHECK();
+    uint32_t *kin = U(L.k0), *vin = d_perm, *kout = U(L.k1), *vout = U(L.v1);
+    for (int p = 0; p < 4; ++p) {
+        if (launch_onesweep<8>(L.parts, s, kin, vin, kout, vout, &hdr->n_vis, 8 * p, U(L.hist) + kHistSlot * p,
+                               U(L.st) + p * L.st_stride, &hdr->ctr[p], &hdr->err) != cudaSuccess) {
+            cudaGetLastError();
+            return GS_ERR_CUDA;
+        }
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    return GS_OK;
+}
+
+extern "C" gs_status gs_gather_rows(void *stream, int32_t n, int32_t row_bytes, const void *d_src,
+                                    const uint32_t *d_perm, void *d_dst)
+{
+    if (n < 0 || row_bytes <= 0 || (row_bytes & 3)) return GS_ERR_ARG;
+    if (n == 0) return GS_OK;
+    if (!d_src || !d_perm || !d_dst || ((uintptr_t)d_src & 3) || ((uintptr_t)d_dst & 3) ||
+        ((uintptr_t)d_perm & 3))
+        return GS_ERR_ARG;
+    const int words = row_bytes / 4;
+    const int64_t total = (int64_t)n * words;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 148 * 16);
+    gather_rows_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(total, words, static_cast<const uint32_t *>(d_src),
+                                                           d_perm, n, static_cast<uint32_t *>(d_dst));
+    count_launch();
+    GS_LAUNCH_CHECK();
+    return GS_OK;
+}

@@ -31,6 +31,27 @@ def activate(scene: dict, device="cuda") -> dict:
             "sh": t(scene["sh"]), "sh_degree": int(scene["sh_degree"])}
 
 
+def spatial_order(scene: dict, keys=("means", "scales", "quats", "opacities", "sh", "log_scales",
+                                      "opacity_logits")) -> tuple[dict, torch.Tensor]:
+    """The scene's splats stored along a Z-order curve of their means (a
+    one-time preparation when a scene is loaded; gs_spatial_order +
+    gs_gather_rows on the GPU). Returns the reordered scene (device tensors,
+    other entries passed through) and the permutation: new row k is old row
+    perm[k]. Images are unchanged except where two splats meet in a tile at
+    exactly equal depth."""
+    dev = torch.device("cuda")
+    means = torch.as_tensor(scene["means"], dtype=torch.float32, device=dev).contiguous()
+    perm = api.gs_spatial_order(means)
+    out = {}
+    for k, v in scene.items():
+        if k in keys:
+            t = torch.as_tensor(v, device=dev).contiguous()
+            out[k] = api.gs_gather_rows(t, perm)
+        else:
+            out[k] = v
+    return out, perm
+
+
 class Rasterizer:
     """Renders P splats into a fixed list of cameras (at most 64)."""
 

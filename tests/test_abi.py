@@ -142,4 +142,18 @@ def test_host_argument_checks(L):
     assert lb.gs_fma_peak(None, 2, 1, 10, ptr, C.byref(flop)) == GS_ERR_ARG
     assert lb.gs_fma_peak(None, 0, 1, 0, ptr, C.byref(flop)) == GS_ERR_ARG
     assert lb.gs_fma_peak(None, 1, 1, 10, None, C.byref(flop)) == GS_ERR_ARG
+    # scene preparation: sizes, null / misaligned pointers; P = 0 and n = 0 do nothing
+    assert lb.gs_spatial_order_workspace_bytes(-1) == 0
+    assert lb.gs_spatial_order_workspace_bytes(1000) > 1000 * 12
+    assert lb.gs_spatial_order(None, -1, ptr, ptr, ptr) == GS_ERR_ARG
+    assert lb.gs_spatial_order(None, 1 << 30, ptr, ptr, ptr) == GS_ERR_ARG
+    assert lb.gs_spatial_order(None, 10, None, ptr, ptr) == GS_ERR_ARG
+    assert lb.gs_spatial_order(None, 10, ptr, C.c_void_p(260), ptr) == GS_ERR_ARG
+    assert lb.gs_spatial_order(None, 0, None, None, None) == 0
+    assert lb.gs_gather_rows(None, 10, 6, ptr, ptr, ptr) == GS_ERR_ARG
+    assert lb.gs_gather_rows(None, 10, 0, ptr, ptr, ptr) == GS_ERR_ARG
+    assert lb.gs_gather_rows(None, -1, 4, ptr, ptr, ptr) == GS_ERR_ARG
+    assert lb.gs_gather_rows(None, 10, 4, ptr, None, ptr) == GS_ERR_ARG
+    assert lb.gs_gather_rows(None, 10, 4, C.c_void_p(258), ptr, ptr) == GS_ERR_ARG
+    assert lb.gs_gather_rows(None, 0, 4, None, None, None) == 0
     assert lb.gs_status_string(4) == b"overlap capacity exceeded"
