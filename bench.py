@@ -41,9 +41,9 @@ SMS, FP32_LANES = 148, 128
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
 #       --clock-control none -k regex:render_kernel -c 2
 #       python bench.py --profile poly1 --steps 2 --warmup 1
-# (1448162816 read + 649723648 written); set to None whenever the blend
-# kernel changes until it is captured again.
-BLEND_TRAFFIC = 1448162816 + 649723648
+# (731202048 read + 628587776 written, scene stored in Z-order); set to None
+# whenever the blend kernel changes until it is captured again.
+BLEND_TRAFFIC = 731202048 + 628587776
 
 
 def hbm_peak_gbs() -> tuple[float, str]:
@@ -82,7 +82,7 @@ def binsort_bytes(r) -> dict:
 # (1M splats, 4 cameras at 1920x1080; the kernel's code, not the scene, sets
 # these): the FMA-pipe fraction the metric asks for, beside the FLOP-based
 # roofline fraction. Reset with BLEND_TRAFFIC when the blend changes.
-BLEND_NCU = {"issue_active": 0.783, "fma_pipe": 0.342, "alu_pipe": 0.466, "lanes_active_of_32": 15.7,
+BLEND_NCU = {"issue_active": 0.796, "fma_pipe": 0.348, "alu_pipe": 0.475, "lanes_active_of_32": 15.7,
              "source": "ncu --set full, render_kernel<POLY1, 4, FP32>, 1M splats x 4 cameras"}
 
 
@@ -108,7 +108,7 @@ def load_scene(a, P: int, seed: int = 0):
 def _default_workload(a) -> bool:
     """The configuration BLEND_TRAFFIC was captured on."""
     return ((a.splats, a.cams, a.width, a.height) == (3_000_000, 16, 1920, 1080)
-            and not a.tile and not a.ppt and not a.rect)
+            and not a.tile and not a.ppt and not a.rect and getattr(a, "splat_order", "zorder") == "zorder")
 
 
 def fma_peak_tflops(half2: bool) -> float:
