@@ -319,7 +319,9 @@ def run_reference(a, world, rank):
             "data": "synthetic", "config": workload(a),
             "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle",
                              "sample": desc.replace("camera 0", "camera k") +
-                             "; one step = one such sample per camera"},
+                             "; one step = one such sample per camera; the oracle reads the "
+                             "splats in the generator's order (its time does not depend on "
+                             "the storage order)"},
             "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
