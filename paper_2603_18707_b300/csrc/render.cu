@@ -131,8 +131,12 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
         ne[k] = n;
         if (px0 + k < cm.W && py < cm.H) active |= 1u << k;
         // the alpha a pixel takes: eps while it is active, never once it
-        // stopped (one compare per pixel and entry instead of a mask test)
+        // stopped (one compare per pixel and entry instead of a mask test).
+        // FP32: a pixel that is off the frame or stopped gets x = NaN, so its
+        // Q and alpha are NaN and fail alpha >= eps (no threshold register).
+        // FP16x2 keeps a threshold: its min with alpha_max drops a NaN.
         ek[k] = (active >> k & 1u) ? eps : INFINITY;
+        if (!HALF && !(active >> k & 1u)) xs[k] = NAN;
     }
     const __half2 x0h = __float2half2_rn(fminf(cfg.x0, 60000.f)), amaxh = __float2half2_rn(amax);
     // the FP16x2 alphas carry ~1e-3 absolute error: skip only far below eps
@@ -211,7 +215,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
             if constexpr (blend_branchless<KIND>()) {
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    const bool use = al[k] >= ek[k];
+                    const bool use = al[k] >= (HALF ? ek[k] : eps);
                     const float a = fminf(amax, al[k]);
                     const float Tn = fmaf(-a, T[k], T[k]);
                     const bool stop = use && Tn < tmin;
@@ -224,17 +228,23 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                     lastc[k] = add ? pos : lastc[k];
                     ne[k] = stop ? pos : ne[k];
                     active &= ~((unsigned)stop << k);
-                    ek[k] = stop ? INFINITY : ek[k];
+                    if (HALF)
+                        ek[k] = stop ? INFINITY : ek[k];
+                    else
+                        xs[k] = stop ? NAN : xs[k];
                 }
             } else {
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    if (!(al[k] >= ek[k])) continue;
+                    if (!(al[k] >= (HALF ? ek[k] : eps))) continue;
                     al[k] = fminf(amax, al[k]);
                     const float Tn = fmaf(-al[k], T[k], T[k]);
                     if (Tn < tmin) {
                         active &= ~(1u << k);
-                        ek[k] = INFINITY;
+                        if (HALF)
+                            ek[k] = INFINITY;
+                        else
+                            xs[k] = NAN;
                         ne[k] = pos;
                         continue;
                     }
