@@ -51,7 +51,10 @@ constexpr int kSpinLimit = 1 << 20;
 #define GS_LOOK_WINDOW 1
 #endif
 #ifndef GS_EMIT_MIN_BLOCKS
-#define GS_EMIT_MIN_BLOCKS 4 // 0: no register cap from the occupancy target; 4 measured fastest
+// 0: no register cap from the occupancy target. 8 (32 registers, some
+// spills to L1) measured fastest: the emission waits on memory, and 8 CTAs
+// per SM hide more of it than 4 (64 registers, no spills) or 6.
+#define GS_EMIT_MIN_BLOCKS 8
 #endif
 #if GS_EMIT_MIN_BLOCKS
 #define GS_EMIT_BOUNDS __launch_bounds__(256, GS_EMIT_MIN_BLOCKS)
