@@ -180,7 +180,8 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                 const float umid = fmaf(a.x, xmid, ub);
                 const float um = fmaxf(fmaf(-0.5f * (PPT - 1), a.x, fabsf(umid)), 0.f);
 #else
-                const float ua = fmaf(a.x, xs[0], ub), uz = fmaf(a.x, xs[PPT - 1], ub);
+                // the run's ends (not xs[], which is NaN for stopped pixels)
+                const float ua = fmaf(a.x, lx + 0.5f, ub), uz = fmaf(a.x, lx + PPT - 0.5f, ub);
                 const float um = ((ua > 0.f) != (uz > 0.f)) ? 0.f : fminf(fabsf(ua), fabsf(uz));
 #endif
                 if constexpr (!HALF && (KIND == GS_K_POLY1 || KIND == GS_K_EXP)) {
