@@ -157,3 +157,14 @@ def test_host_argument_checks(L):
     assert lb.gs_gather_rows(None, 10, 4, C.c_void_p(258), ptr, ptr) == GS_ERR_ARG
     assert lb.gs_gather_rows(None, 0, 4, None, None, None) == 0
     assert lb.gs_status_string(4) == b"overlap capacity exceeded"
+
+
+def test_missing_library_fails_loudly(L, monkeypatch):
+    """No CPU fallback: without the built library every entry point raises."""
+    from paper_2603_18707_b300 import _lib, api
+    monkeypatch.setattr(_lib, "LIB_PATH", os.path.join(ROOT, "no_such_dir", "libgs_b300.so"))
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        _lib.lib()
+    with pytest.raises(RuntimeError, match="missing"):
+        api.make_config("poly1", "opacity")
