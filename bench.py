@@ -358,16 +358,18 @@ def run_ours(a, world, rank, local):
         r.forward(sc, n_eval=False)
         torch.cuda.synchronize()
         e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        l0 = api.gs_launch_count()
         e[0].record()
         for _ in range(a.steps):
             r.run_async(sc)
         e[1].record()
         torch.cuda.synchronize()
+        per_step = (api.gs_launch_count() - l0) / max(a.steps, 1)
         if rank == 0:
             print(json.dumps({"profile": a.profile, "steps": a.steps, "config": workload(a),
                               "overrides": over, "ms_per_step": e[0].elapsed_time(e[1]) / max(a.steps, 1),
                               "records_drawn_overlaps": list(r.n_records()),
-                              "launches_per_step": 14}), flush=True)
+                              "launches_per_step": per_step}), flush=True)
         return
     def make(kind):
         cfg = api.make_config(kind, "opacity", **over)
