@@ -61,8 +61,9 @@ def binsort_bytes(r) -> dict:
     its record and overlap counts: compaction reads the tile count of every
     record (4 B) and the depth key of every drawn one (4 B) and writes
     (key, id) (8 B); four 8-bit depth passes read and write 16 B per drawn
-    record each; emission reads the id (4 B) and the tile rectangle and
-    count (12 B) per drawn record and writes (tile, id) (8 B) per overlap;
+    record each; emission reads the id (4 B) and the tile rectangle (8 B,
+    whose area is the tile count) per drawn record and writes (tile, id)
+    (8 B) per overlap;
     each tile pass reads and writes 16 B per overlap; the ranges kernel
     reads 4 B per overlap and writes 8 B per tile. For comparison, the
     3DGS design (one LSD sort of 64-bit (tile | depth) keys with 32-bit
@@ -72,7 +73,7 @@ def binsort_bytes(r) -> dict:
         drawn, over = p.n_records()
         bits = max(1, (p.total_tiles - 1).bit_length())
         tile_passes = max(1, (bits + 8) // 9)
-        ours += (4 * p.ncam * p.P + (12 + 4 * 16 + 16) * drawn
+        ours += (4 * p.ncam * p.P + (12 + 4 * 16 + 12) * drawn
                  + (8 + 16 * tile_passes + 4) * over + 8 * p.total_tiles)
         ref += (12 + 24 * math.ceil((bits + 32) / 8)) * over
     return {"ours": ours, "3dgs_design": ref}
