@@ -184,8 +184,10 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                 const float ua = fmaf(a.x, lx + 0.5f, ub), uz = fmaf(a.x, lx + PPT - 0.5f, ub);
                 const float um = ((ua > 0.f) != (uz > 0.f)) ? 0.f : fminf(fabsf(ua), fabsf(uz));
 #endif
-                if constexpr (!HALF && (KIND == GS_K_POLY1 || KIND == GS_K_EXP)) {
-                    if (fmaf(um, um, v2) > b.w) continue; // beyond the record's cut x_cut
+                if constexpr (KIND == GS_K_POLY1 || KIND == GS_K_EXP) {
+                    // beyond the record's cut x_cut: no pixel's exact alpha
+                    // reaches eps (FP16x2 too: it then skips what FP32 skips)
+                    if (fmaf(um, um, v2) > b.w) continue;
                 } else {
                     if (alpha_of_q<KIND>(cfg, b, p3, fmaf(um, um, v2)) < eps_skip) continue;
                 }
