@@ -30,8 +30,8 @@ def _small_scene(P=48, seed=4):
             "sh_degree": 3}
 
 
-def _gpu_grads(api, render, raw, cams, kind, cull, w, bg):
-    cfg = api.make_config(kind, cull)
+def _gpu_grads(api, render, raw, cams, kind, cull, w, bg, **over):
+    cfg = api.make_config(kind, cull, **over)
     sc = render.activate(raw)
     R = render.Rasterizer(cams, cfg, raw["means"].shape[0])
     R.forward(sc, bg)
@@ -85,6 +85,23 @@ def test_backward_matches_oracle_reverse_pass(gs, orc, kind, cull):
     w = _masked_weights(orc, sc, oc, kind, (48, 56, 3))
     gpu, _ = _gpu_grads(api, render, raw, [cam], kind, cull, w, bg)
     ref = orc.render_backward(sc, oc, orc.make_config(kind, KIND_COEFFS[kind], cull), w, bg)
+    _check(gpu, ref)
+
+
+@pytest.mark.parametrize("tile", [(8, 8), (32, 8), (32, 16)])
+def test_backward_tile_shapes(gs, orc, tile):
+    """The reverse pass runs two pixels per thread on every tile shape up to
+    512 pixels (256 threads for 32x16) and its gradients do not depend on
+    the tiling: they match the oracle's tile-free reverse pass."""
+    api, render, synth = gs
+    raw = _small_scene()
+    cam = synth.look_at([0.3, -0.2, -2.5], [0, 0, 0], 56, 48, 60.0)
+    oc = orc.camera_from_dict(cam)
+    sc = _oracle_inputs(orc, raw)
+    bg = (0.2, 0.4, 0.1)
+    w = _masked_weights(orc, sc, oc, "poly1", (48, 56, 3))
+    gpu, _ = _gpu_grads(api, render, raw, [cam], "poly1", "opacity", w, bg, tile=tile)
+    ref = orc.render_backward(sc, oc, orc.make_config("poly1", KIND_COEFFS["poly1"], "opacity"), w, bg)
     _check(gpu, ref)
 
 
