@@ -440,6 +440,11 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
         k[j] = ok ? keys_in[idx] : 0xffffffffu; // invalid keys rank last (top digit, highest index)
         v[j] = ok ? vals_in[idx] : 0u;
     }
+    // this thread's digits' global counts, loaded now so that the latency
+    // overlaps the ranking
+    uint32_t hv[DPT];
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) hv[q] = hist[tid * DPT + q];
     // rank within the warp: match lanes with equal digits
     const uint32_t lt = lanemask_lt();
     uint32_t *wh = s_whist + warp * R;
@@ -459,7 +464,7 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
     }
     __syncthreads();
     // per digit: warp-exclusive offsets and block counts
-    uint32_t cnt[DPT], csum = 0, hsum = 0, hv[DPT];
+    uint32_t cnt[DPT], csum = 0, hsum = 0;
 #pragma unroll
     for (int q = 0; q < DPT; ++q) {
         const int d = tid * DPT + q;
@@ -472,7 +477,6 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
         }
         cnt[q] = c;
         csum += c;
-        hv[q] = hist[d];
         hsum += hv[q];
     }
     uint32_t tot;
