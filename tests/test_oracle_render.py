@@ -44,6 +44,87 @@ def test_sh_basis_orthonormal(orc):
     assert np.allclose(G, np.eye(16), atol=1e-12)
 
 
+def _real_sh_from_scipy(degree, d):
+    """Real SH built independently from scipy's complex Y_l^m (which carries
+    the Condon-Shortley phase): m = 0 -> Y_l^0; m > 0 -> sqrt(2) Re Y_l^m;
+    m < 0 -> sqrt(2) Im Y_l^|m|; bands in order m = -l .. l."""
+    from scipy.special import sph_harm_y
+    theta = math.acos(max(-1.0, min(1.0, d[2])))
+    phi = math.atan2(d[1], d[0]) % (2 * math.pi)
+    out = []
+    for l in range(degree + 1):
+        for m in range(-l, l + 1):
+            y = complex(sph_harm_y(l, abs(m), theta, phi))
+            out.append(y.real if m == 0 else math.sqrt(2) * (y.real if m > 0 else y.imag))
+    return np.array(out)
+
+
+def test_sh_basis_matches_scipy_real_harmonics(orc):
+    """Order and sign of every basis function within each band, against
+    real harmonics assembled from scipy's associated-Legendre based Y_l^m
+    (orthonormality alone would accept a swapped order or a flipped sign)."""
+    rng = np.random.default_rng(7)
+    for _ in range(50):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        assert orc.sh_basis(3, d) == pytest.approx(_real_sh_from_scipy(3, d), abs=1e-13)
+
+
+def test_sh_basis_worked_directions(orc):
+    """Hand values: along +z only the m = 0 functions survive,
+    sqrt((2l+1)/(4 pi)); along +x band 1 is (0, 0, -sqrt(3/(4 pi))) and
+    along +y it is (-sqrt(3/(4 pi)), 0, 0) (3DGS's -y, z, -x order)."""
+    Yz = orc.sh_basis(3, [0.0, 0.0, 1.0])
+    want = np.zeros(16)
+    for l, k in ((0, 0), (1, 2), (2, 6), (3, 12)):
+        want[k] = math.sqrt((2 * l + 1) / (4 * math.pi))
+    assert Yz == pytest.approx(want, abs=1e-15)
+    c1 = math.sqrt(3 / (4 * math.pi))
+    assert orc.sh_basis(1, [1.0, 0.0, 0.0])[1:] == pytest.approx([0.0, 0.0, -c1], abs=1e-15)
+    assert orc.sh_basis(1, [0.0, 1.0, 0.0])[1:] == pytest.approx([-c1, 0.0, 0.0], abs=1e-15)
+    # band 2 at (x, y, z) = (1, 1, 0)/sqrt(2): xy term 0.5 sqrt(15/pi) / 2, (x^2 - y^2) term 0
+    Y = orc.sh_basis(2, [1 / math.sqrt(2), 1 / math.sqrt(2), 0.0])
+    assert Y[4] == pytest.approx(0.25 * math.sqrt(15 / math.pi), abs=1e-15)
+    assert Y[8] == pytest.approx(0.0, abs=1e-15)
+
+
+def test_projection_jacobian_clamped_outside_frustum(orc):
+    """Means whose tx/tz or ty/tz lie beyond 1.3 tan(fov/2) (3DGS): Sigma'
+    uses the pinhole Jacobian at the clamped point (tx, ty clamped to
+    +-1.3 tan(fov/2) tz, same depth), taken here numerically from the plain
+    pinhole map, while mu' stays the unclamped projection. The unclamped
+    numerical Jacobian gives a different Sigma' (the branch is reached)."""
+    cam = _cam(orc, 80, 60, fov=60.0)
+    vm = np.array(cam.viewmat[:]).reshape(4, 4)
+    R, tv = vm[:3, :3], vm[:3, 3]
+    limx, limy = 1.3 * 0.5 * cam.width / cam.fx, 1.3 * 0.5 * cam.height / cam.fy
+    rng = np.random.default_rng(5)
+    h = 1e-6
+    for ux, uy in ((2.0, 0.1), (-1.5, -0.2), (0.2, 1.4), (-0.1, -2.5), (1.9, -1.7)):
+        tz = 2.5
+        t = np.array([ux * tz, uy * tz, tz])
+        mu = R.T @ (t - tv)
+        s = np.exp(rng.normal(-2.5, 0.3, 3))
+        q = rng.normal(size=4)
+        out = orc.splats_to_numpy(orc.project(_one_splat(mu, s, q), cam,
+                                              orc.make_config("exp", (), "universal")), 1)
+        Rm = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+        Sig = Rm @ np.diag(s * s) @ Rm.T
+        tc = np.array([np.clip(ux, -limx, limx) * tz, np.clip(uy, -limy, limy) * tz, tz])
+        mc = R.T @ (tc - tv)
+
+        def jac(p):
+            return np.stack([(_pinhole(cam, p + h * e) - _pinhole(cam, p - h * e)) / (2 * h)
+                             for e in np.eye(3)], axis=1)
+
+        Jc, Ju = jac(mc), jac(mu)
+        Sc, Su = Jc @ Sig @ Jc.T, Ju @ Sig @ Ju.T
+        got = out["cov2d"][0]
+        assert got == pytest.approx([Sc[0, 0], Sc[0, 1], Sc[1, 1]], rel=1e-6, abs=1e-9)
+        assert not np.allclose(got, [Su[0, 0], Su[0, 1], Su[1, 1]], rtol=1e-3, atol=0)
+        assert out["mean2d"][0] == pytest.approx(_pinhole(cam, mu), abs=1e-9)
+
+
 def test_projection_on_axis_identity_rotation(orc):
     """Identity quaternion => Sigma = diag(s^2); on the optical axis
     J = diag(f/z) so Sigma' = diag((f s_x / z)^2, (f s_y / z)^2)."""
