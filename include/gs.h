@@ -233,24 +233,32 @@ gs_status gs_render_backward(void *stream, const gs_camera *cams, int32_t ncam, 
  *
  * Same arguments, results and errors as gs_bin_sort, minus the workspace: the
  * scratch is one fixed array of GS_NOALLOC_WORKSPACE_BYTES in static device
- * memory, reserved on every GPU that loads the library and held until the
- * process exits. The call itself allocates nothing. Sizes whose workspace
+ * memory, held until the process exits. Sizes whose workspace
  * (gs_bin_sort_workspace_bytes(ncam * P, capacity, tiles): about 17 bytes
  * per record plus 13 bytes per overlap of capacity) would not fit are
  * rejected with GS_ERR_ARG before anything is launched.
- *  - The first call on a device looks up the array's device address (with
- *    that device current) and caches it: make that first call before any
- *    stream capture.
+ *  - Set-up happens in the first call on each device: with that device
+ *    current it looks up the array's device address and caches it. Under
+ *    CUDA's lazy module loading (the default) that lookup is also what loads
+ *    this part of the library's device code, and with it reserves the array:
+ *    the first call can therefore allocate, take time, and fail with
+ *    GS_ERR_CUDA if the device is out of memory. Make that first call at
+ *    set-up time (a call with P = 0 is enough), before any stream capture and
+ *    before the loop that must not allocate. Later calls allocate nothing.
  *  - All calls on a device share the one array; each call clears the parts
  *    that must start at zero. Calls that overlap on the GPU (other streams,
  *    or host threads without ordering between them) race: serialise them.
- *  - The device error word lives inside the static array; detect an
- *    overflowing capacity from d_count (overlaps counted > capacity). */
+ *  - d_error (optional, may be NULL): uint32, device or pinned host memory;
+ *    receives, stream-ordered at the end of the call, the device error word
+ *    of this call (OR of GS_ERR_CAPACITY and GS_ERR_TIMEOUT, 0 if none).
+ *    The word lives in the shared array, so gs_workspace_status cannot reach
+ *    it: without d_error a timed-out wait goes unseen (an overflowing
+ *    capacity still shows in d_count: overlaps counted > capacity). */
 #define GS_NOALLOC_WORKSPACE_BYTES ((size_t)32 << 20)
 gs_status gs_bin_sort_noalloc(void *stream, const gs_camera *cams, int32_t ncam, int32_t P,
                               const gs_config *cfg, const void *d_splat2d, int64_t capacity,
                               uint32_t *d_vals, uint32_t *d_ranges, uint64_t *d_keys64,
-                              uint32_t *d_count);
+                              uint32_t *d_count, uint32_t *d_error);
 
 /* Reads (synchronously, on `stream`) the device error word of a bin/sort
  * workspace into *code (OR of GS_ERR_CAPACITY / GS_ERR_TIMEOUT) and clears

@@ -57,7 +57,7 @@ _SIGS = {
     "gs_bin_sort": (_i32, [_vp, C.POINTER(GsCamera), _i32, _i32, C.POINTER(GsConfig), _vp, _i64,
                            _vp, _sz, _vp, _vp, _vp, _vp]),
     "gs_bin_sort_noalloc": (_i32, [_vp, C.POINTER(GsCamera), _i32, _i32, C.POINTER(GsConfig), _vp,
-                                   _i64, _vp, _vp, _vp, _vp]),
+                                   _i64, _vp, _vp, _vp, _vp, _vp]),
     "gs_render_work_bytes": (_sz, []),
     "gs_render": (_i32, [_vp, C.POINTER(GsCamera), _i32, _i32, C.POINTER(GsConfig), _vp, _vp, _vp,
                          C.POINTER(C.c_float), _vp, _vp, _vp, _vp, _vp]),

@@ -127,14 +127,15 @@ def gs_bin_sort(cams, P, cfg, splat2d, capacity, workspace, vals, ranges, keys64
 
 
 def gs_bin_sort_noalloc(cams, P, cfg, splat2d, capacity, vals, ranges, keys64=None, count=None,
-                        stream=None):
+                        error=None, stream=None):
     """gs_bin_sort for callers that cannot allocate device memory: the
     scratch is the library's static device array (GS_NOALLOC_WORKSPACE_BYTES),
-    shared by every call on a device."""
+    shared by every call on a device. error: optional uint32 buffer that
+    receives this call's device error word."""
     arr = camera_array(cams)
     check("gs_bin_sort_noalloc", lib().gs_bin_sort_noalloc(
         _stream(stream), arr, len(arr), int(P), C.byref(cfg), _p(splat2d), int(capacity),
-        _p(vals), _p(ranges), _p(keys64), _p(count)))
+        _p(vals), _p(ranges), _p(keys64), _p(count), _p(error)))
 
 
 def gs_render_work_bytes() -> int:

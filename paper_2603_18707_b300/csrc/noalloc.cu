@@ -5,8 +5,11 @@
 // real-time frame loop whose rules forbid allocating (and the stalls that come
 // with it) once it is running. gs_bin_sort needs a scratch workspace from the
 // caller; this variant brings its own instead: a fixed array in static device
-// memory, reserved when the library is loaded on a device and held until the
-// process exits. The caller still passes every input and output buffer.
+// memory, held until the process exits. The array is reserved when this
+// file's device code is loaded on a device; under CUDA's lazy module loading
+// that is the first cudaGetSymbolAddress below, i.e. the first call on the
+// device, which callers make at set-up time. The caller still passes every
+// input and output buffer.
 #include <mutex>
 
 #include "gs_common.cuh"
@@ -51,7 +54,7 @@ gs_status scratch_for_current_device(void **out)
 extern "C" gs_status gs_bin_sort_noalloc(void *stream, const gs_camera *cams, int32_t ncam, int32_t P,
                                          const gs_config *cfg, const void *d_splat2d,
                                          int64_t capacity, uint32_t *d_vals, uint32_t *d_ranges,
-                                         uint64_t *d_keys64, uint32_t *d_count)
+                                         uint64_t *d_keys64, uint32_t *d_count, uint32_t *d_error)
 {
     if (!cams || !cfg || ncam <= 0 || ncam > GS_MAX_CAMERAS || P < 0 || capacity < 0) return GS_ERR_ARG;
     const int64_t tiles = gs_total_tiles(cams, ncam, cfg);
@@ -61,7 +64,12 @@ extern "C" gs_status gs_bin_sort_noalloc(void *stream, const gs_camera *cams, in
     void *ws = nullptr;
     const gs_status st = scratch_for_current_device(&ws);
     if (st != GS_OK) return st;
-    // gs_bin_sort clears the zero-initialised part of the workspace itself.
-    return gs_bin_sort(stream, cams, ncam, P, cfg, d_splat2d, capacity, ws, kNoAllocBytes, d_vals,
-                       d_ranges, d_keys64, d_count);
+    // gs_bin_sort clears the zero-initialised part of the workspace itself
+    // (the error word included, so the word read below is this call's).
+    const gs_status rs = gs_bin_sort(stream, cams, ncam, P, cfg, d_splat2d, capacity, ws, kNoAllocBytes,
+                                     d_vals, d_ranges, d_keys64, d_count);
+    if (rs != GS_OK || !d_error) return rs;
+    // the error word sits at the start of the workspace; hand it out, since
+    // the caller cannot name the static array
+    return gs_workspace_status_async(stream, ws, d_error);
 }
