@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import ctypes
+import hashlib
 import json
 import math
 import os
@@ -30,20 +31,37 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "frames/s and Gsplat-evals/s, poly-1+opacity-cull vs exp on same B300 at ≥45 dB vs exp"
-# FP32 FLOPs of one splat evaluation (FMA = 2): dx, dy (2); Q = A dx^2 +
-# 2 B dx dy + C dy^2 (7); kernel and opacity: f1 c0 + c1 Q and o' * (3),
-# exp -Q/2 and o' * (2, plus one MUFU ex2); blend T (1 - a), a T,
-# C += c a T (9).
-FLOP_PER_EVAL = {"poly1": 21, "exp": 20}
+# FLOPs of one splat evaluation (FMA = 2), counted as the method states the
+# work: dx, dy (2); Q = A dx^2 + 2 B dx dy + C dy^2 as one FMUL and two FFMA
+# (5); the opacity-folded kernel, f1 one FFMA (2), f'2 two (4), f3 three (6),
+# exp one FMUL plus a MUFU ex2 (1); w = alpha T (1); C += w c (6); T (1 - alpha)
+# (2). f1: 18. The FP16x2 variant runs Q and the kernel in packed half.
+FLOP_PER_EVAL = {"poly1": 18, "poly2": 20, "poly3": 22, "exp": 17}
+HALF_FLOP_PER_EVAL = {"poly1": 7, "poly2": 9, "poly3": 11, "exp": 6}
 SMS, FP32_LANES = 148, 128
-# DRAM bytes (read + write) of one f1 blend launch (render_kernel<1, 4, 0>) on
-# the default workload (3M splats, 16 cameras at 1920x1080), from
+BLEND_SOURCES = ("render.cu", "blend_math.cuh", "gs_common.cuh")
+
+
+def blend_source_hash() -> str:
+    """Hash of the sources the blend kernel is compiled from: the ncu figures
+    below belong to the kernel they were captured on and are reported only
+    while this hash matches theirs."""
+    h = hashlib.sha256()
+    for f in BLEND_SOURCES:
+        with open(os.path.join(ROOT, "paper_2603_18707_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# ncu figures of the f1 blend (render_kernel<POLY1, 4, FP32>): DRAM bytes (read
+# + write) of one launch on the default workload (3M splats, 16 cameras at
+# 1920x1080, scene in Z-order), from
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
 #       --clock-control none -k regex:render_kernel -c 2
 #       python bench.py --profile poly1 --steps 2 --warmup 1
-# (731269120 read + 628371456 written, scene stored in Z-order); set to None
-# whenever the blend kernel changes until it is captured again.
-BLEND_TRAFFIC = 731269120 + 628371456
+# and pipe utilisation from a --set full capture of the same kernel (1M
+# splats x 4 cameras; the kernel's code, not the scene, sets these).
+BLEND_CAPTURE = {"src_hash": None, "traffic": None, "ncu": None}
 
 
 def hbm_peak_gbs() -> tuple[float, str]:
@@ -79,14 +97,6 @@ def binsort_bytes(r) -> dict:
     return {"ours": ours, "3dgs_design": ref}
 
 
-# Pipe utilisation of the same blend kernel from its full-section ncu capture
-# (1M splats, 4 cameras at 1920x1080; the kernel's code, not the scene, sets
-# these): the FMA-pipe fraction the metric asks for, beside the FLOP-based
-# roofline fraction. Reset with BLEND_TRAFFIC when the blend changes.
-BLEND_NCU = {"issue_active": 0.795, "fma_pipe": 0.343, "alu_pipe": 0.464, "lanes_active_of_32": 15.75,
-             "source": "ncu --set full, render_kernel<POLY1, 4, FP32>, 1M splats x 4 cameras"}
-
-
 def load_scene(a, P: int, seed: int = 0):
     """The cluster scene (SH degree 3), activated on the GPU and, unless
     --splat-order input, stored in Z-order of the means (render.spatial_order,
@@ -107,7 +117,7 @@ def load_scene(a, P: int, seed: int = 0):
 
 
 def _default_workload(a) -> bool:
-    """The configuration BLEND_TRAFFIC was captured on."""
+    """The configuration BLEND_CAPTURE's traffic was captured on."""
     return ((a.splats, a.cams, a.width, a.height) == (3_000_000, 16, 1920, 1080)
             and not a.tile and not a.ppt and not a.rect and getattr(a, "splat_order", "zorder") == "zorder")
 
@@ -148,6 +158,7 @@ def parse():
     p.add_argument("--no-fp16", action="store_true", help="skip the FP16x2 precision leg")
     p.add_argument("--no-f2range", action="store_true", help="skip the range-extended f2 leg")
     p.add_argument("--no-tensor", action="store_true", help="skip the tensor-core quadric leg")
+    p.add_argument("--no-sweep", action="store_true", help="skip the kernel x cull sweep")
     p.add_argument("--splat-order", choices=["zorder", "input"], default="zorder",
                    help="store the scene in Z-order of the means once at load (default) or keep "
                         "the generator's order")
@@ -272,10 +283,11 @@ def sum_over_ranks(x: float, world: int) -> float:
 # CPU oracle timing (cpu_baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(raw, cam, n_tiles: int, seed: int = 0):
+def oracle_sample(raw, cam, n_tiles: int, seed: int = 0, with_image: bool = False):
     """Times the FP64 oracle on one camera: projection of every splat plus
     the tile-binned render of n_tiles tiles. Returns (frame seconds
-    extrapolated to all tiles, sample seconds, description)."""
+    extrapolated to all tiles, sample seconds, description) and, with
+    with_image, the oracle image and the sampled tile ids."""
     import numpy as np
     import oracle
     oc = oracle.camera_from_dict(cam)
@@ -289,12 +301,24 @@ def oracle_sample(raw, cam, n_tiles: int, seed: int = 0):
     t0 = time.perf_counter()
     s2d = oracle.project(sc, oc, cfg)
     t1 = time.perf_counter()
-    oracle.render_tiled(sc, oc, cfg, tiles=tiles, s2d=s2d)
+    img, *_ = oracle.render_tiled(sc, oc, cfg, tiles=tiles, s2d=s2d)
     t2 = time.perf_counter()
     frame = (t1 - t0) + (t2 - t1) * (tx * ty) / n_tiles
     desc = (f"FP64 oracle, camera {seed % 16}: projection of all {sc['means'].shape[0]} splats + "
             f"tile-binned render of {n_tiles} of {tx * ty} tiles, extrapolated to the frame")
+    if with_image:
+        return frame, t2 - t0, desc, img, tiles
     return frame, t2 - t0, desc
+
+
+def oracle_tiles(raw, cam, kind, tiles):
+    """The FP64 oracle's tile render of one camera for a kernel (CPU-baseline
+    leg): the image, with only the given tiles rendered."""
+    import oracle
+    co = json.load(open(os.path.join(ROOT, "tests", "golden", "coeffs.json")))[kind]
+    cfg = oracle.make_config(kind, co, "opacity")
+    img, *_ = oracle.render_tiled(oracle.activate(raw), oracle.camera_from_dict(cam), cfg, tiles=tiles)
+    return img
 
 
 def run_reference(a, world, rank):
@@ -383,6 +407,9 @@ def run_ours(a, world, rank, local):
     for k, r in R.items():
         r.forward(sc, n_eval=True)  # sizes the overlap buffers, counts evaluations
         evals[k] = int(r.n_eval.to(torch.int64).sum().item())
+    # camera 0's f1 image, for the oracle comparison of the CPU-baseline leg
+    # (the serving leg below renders other poses into the same buffers)
+    img0 = R["poly1"].images()[0].cpu().numpy()
     for ip, ie in zip(R["poly1"].images(), R["exp"].images()):
         mse = torch.mean((ip - ie) ** 2).item()
         psnr.append(-10 * math.log10(max(mse, 1e-30)))
@@ -511,21 +538,30 @@ def run_ours(a, world, rank, local):
     peak = fma_peak_tflops(False)
     blend_s = st["blend_ms"] / 1e3
     achieved = evals["poly1"] * FLOP_PER_EVAL["poly1"] / blend_s / 1e12
+    fresh = BLEND_CAPTURE["src_hash"] == blend_source_hash()
     roofline = {"bound": "alu", "kernel": "blend (render_kernel<POLY1>)", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": BLEND_TRAFFIC if _default_workload(a) else None,
-                "ncu_pipes": BLEND_NCU if _default_workload(a) else None,
+                "traffic": BLEND_CAPTURE["traffic"] if fresh and _default_workload(a) else None,
+                "ncu_pipes": BLEND_CAPTURE["ncu"] if fresh else None,
+                "flop_per_eval": FLOP_PER_EVAL["poly1"],
                 "peak_source": "measured FFMA rate (gs_fma_peak, this run); derived "
                                f"148 SMs x 128 lanes x 2 FLOP x 2032 MHz = {peak_derived:.1f}",
                 "dominant_stage": dom}
 
     extra = {}
+    sweep = None
+    if not a.no_sweep:
+        torch.cuda.empty_cache()
+        try:
+            sweep = bench_sweep(a, sc, cams, over, world, R)
+        except Exception as exc:  # noqa: BLE001 - a failed leg must not lose the headline
+            sweep = {"error": f"{type(exc).__name__}: {exc}"}
     del R, sc
     for name, on, fn in (("differentiable", not a.no_diff, bench_differentiable),
                          ("batched", not a.no_batched, bench_batched),
-                         ("fp16x2", not a.no_fp16, bench_fp16x2),
                          ("f2_range", not a.no_f2range, bench_f2_range),
-                         ("tensor_quadric", not a.no_tensor, bench_tensor_quadric)):
+                         ("tensor_quadric", not a.no_tensor, bench_tensor_quadric),
+                         ("fp16x2", not a.no_fp16, bench_fp16x2)):
         if not on:
             continue
         torch.cuda.empty_cache()
@@ -534,14 +570,23 @@ def run_ours(a, world, rank, local):
         except Exception as exc:  # noqa: BLE001 - a failed extra leg must not lose the headline
             extra[name] = {"error": f"{type(exc).__name__}: {exc}"}
 
-    cpu = None
+    cpu, vs_oracle = None, None
     if rank == 0 and world == 1 and not a.no_cpu:
         import oracle
         oracle.build()
-        frame_s, sample_s, desc = oracle_sample(raw, cams[0], 64)
+        frame_s, sample_s, desc, oimg, otiles = oracle_sample(raw, cams[0], 64, with_image=True)
         cpu = {"value": 1.0 / frame_s, "unit": "frames/s", "cores": os.cpu_count(),
                "kind": "oracle", "sample": desc + f" ({sample_s:.1f} s of CPU time)"}
+        # the headline f1 render against the FP64 oracle's f1 on the same tiles
+        vs_oracle = _vs_oracle(img0, oimg, otiles, a.width)
+        # the FP16x2 leg's camera-0 images against the oracle on those tiles
+        half = extra.get("fp16x2", {}).pop("_cam0", None) if isinstance(extra.get("fp16x2"), dict) else None
+        for kind, im in (half or {}).items():
+            ref = oimg if kind == "poly1" else oracle_tiles(raw, cams[0], kind, otiles)
+            extra["fp16x2"][kind]["vs_oracle"] = _vs_oracle(im, ref, otiles, a.width, per_channel=True)
 
+    if isinstance(extra.get("fp16x2"), dict):
+        extra["fp16x2"].pop("_cam0", None)
     evals_all = {k: sum_over_ranks(float(v), world) for k, v in evals.items()}
     if rank != 0:
         return
@@ -560,7 +605,96 @@ def run_ours(a, world, rank, local):
             "roofline": roofline, "sort_bin_hbm": sort_bin, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches}
     line.update(extra)
+    # compact summaries last (the end of the line is what a truncated log keeps)
+    line["sweep_config2"] = sweep
+    line["quality"] = {
+        "psnr_gpu_f1_vs_oracle_f1_db": vs_oracle,
+        "psnr_f1_vs_exp_db": float(np.mean(psnr)),
+        "psnr_f3_vs_exp_db": (sweep or {}).get("poly3/opacity", [None] * 4)[3] if isinstance(sweep, dict) else None,
+        "note": "f1 is not within 45 dB of exp (the paper claims no such bound); the GPU f1 matches the "
+                "FP64 oracle's f1, and f3 is the order that approaches exp"}
+    line["headline"] = {"frames_per_s": fps, "gsplat_evals_per_s": line["gsplat_evals_per_s"],
+                        "exp_frames_per_s": line["exp"]["frames_per_s"],
+                        "speedup_poly1_vs_exp": line["speedup_poly1_vs_exp"],
+                        "blend_frac_of_ffma": roofline["frac"],
+                        "bin_sort_ms": stages["poly1"]["bin_sort_ms"], "blend_ms": stages["poly1"]["blend_ms"]}
     print(json.dumps(line), flush=True)
+
+
+def _psnr(a, b) -> float:
+    import numpy as np
+    mse = float(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2))
+    return float(-10 * np.log10(max(mse, 1e-30)))
+
+
+def _vs_oracle(img, ref, tiles, width, tile=16, per_channel=False) -> dict:
+    """PSNR and largest per-channel error of a GPU image against the oracle's
+    tile render, over the oracle's sampled tiles."""
+    import numpy as np
+    tx = (width + tile - 1) // tile
+    H = img.shape[0]
+    m = np.zeros(img.shape[:2], bool)
+    for t in tiles:
+        y, x = (t // tx) * tile, (t % tx) * tile
+        m[y:min(y + tile, H), x:x + tile] = True
+    err = np.abs(img[m].astype(np.float64) - ref[m])
+    out = {"psnr_db": _psnr(img[m], ref[m]), "max_abs": float(err.max()),
+           "mean_abs": float(err.mean()), "tiles": len(tiles)}
+    if per_channel:
+        out["max_per_channel"] = [float(v) for v in err.max(0)]
+        out["mean_per_channel"] = [float(v) for v in err.mean(0)]
+    return out
+
+
+SWEEP_ARMS = [(k, c) for k in ("exp", "poly1", "poly2", "poly3") for c in ("universal", "opacity")]
+
+
+def bench_sweep(a, sc, cams, over, world, R_head):
+    """The kernel x cull table on the headline workload (the synthetic
+    analogue of the paper's Table 3 and App. C Table 4): exp, f1, f'2 and f3,
+    each with the universal and the opacity-dependent support, launched like
+    the headline. Per arm: frames/s, Gsplat-evals/s, overlaps (millions),
+    PSNR against the exp render (mean over cameras), blend and bin/sort ms."""
+    import numpy as np
+    import torch
+
+    from paper_2603_18707_b300 import api, render
+    exp_imgs = [im.clone() for im in R_head["exp"].images()]
+    stream = torch.cuda.current_stream()
+    out = {"cols": ["frames_per_s", "gsplat_evals_per_s", "overlaps_M", "psnr_vs_exp_db", "blend_ms",
+                    "bin_sort_ms"]}
+    steps = max(5, a.steps // 4)
+    for kind, cull in SWEEP_ARMS:
+        cfg = api.make_config(kind, cull, **over)
+        r = (render.StreamedRasterizer(cams, cfg, a.splats, groups=a.groups) if a.groups > 1
+             else render.Rasterizer(cams, cfg, a.splats))
+        r.forward(sc, n_eval=True)
+        ev = int(r.n_eval.to(torch.int64).sum().item())
+        psnr = float(np.mean([_psnr(x.cpu().numpy(), y.cpu().numpy()) for x, y in zip(r.images(), exp_imgs)]))
+        for _ in range(3):
+            r.run_async(sc)
+        barrier(world)
+        ms = _events_ms(lambda: r.run_async(sc), steps)
+        ms = max_over_ranks(ms, world)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        acc = [0.0, 0.0]
+        for _ in range(3):
+            r.preprocess(sc)
+            e[0].record(stream)
+            r.bin_sort()
+            e[1].record(stream)
+            r.blend(n_eval=False)
+            e[2].record(stream)
+            torch.cuda.synchronize()
+            acc[0] += e[1].elapsed_time(e[2]) / 3
+            acc[1] += e[0].elapsed_time(e[1]) / 3
+        out[f"{kind}/{cull}"] = [round(world * a.cams / (ms / 1e3), 1),
+                                 round(sum_over_ranks(float(ev), world) / (ms / 1e3) / 1e9, 1),
+                                 round(r.n_records()[1] / 1e6, 2), round(psnr, 2), round(acc[0], 3),
+                                 round(acc[1], 3)]
+        del r
+        torch.cuda.empty_cache()
+    return out
 
 
 def _events_ms(fn, steps):
@@ -646,36 +780,52 @@ def bench_differentiable(a):
 def bench_fp16x2(a):
     """Precision variant on the headline workload (3M splats, 16 cameras,
     1920x1080): f1 and f'2 with the quadric and polynomial in packed FP16x2,
-    colour and transmittance in FP32. Timed like the headline; errors against
-    the FP32 GPU render of the same frames (the FP64-oracle comparison lives
-    in the test suite)."""
+    colour and transmittance in FP32, FP32 decisions within the half alphas'
+    error bound of eps / t_min. Timed like the headline (one stream); errors
+    against the FP32 GPU render of the same frames (the comparison with the
+    FP64 oracle is made by the CPU-baseline leg from the camera-0 images this
+    leg hands back under "_cam0"); the blend's roofline against the measured
+    HFMA2 and FFMA rates (the half share of the evaluation FLOPs at the HFMA2
+    rate, the rest at the FFMA rate)."""
     import numpy as np
     import torch
 
     from paper_2603_18707_b300 import api, render, synth
     raw, sc, _, _ = load_scene(a, a.splats)
     cams = synth.orbit_cameras(a.cams, a.width, a.height)
-    out = {}
+    p32, p16 = fma_peak_tflops(False), fma_peak_tflops(True)
+    out = {"peak_ffma_tflops": p32, "peak_hfma2_tflops": p16, "_cam0": {}}
     for kind in ("poly1", "poly2"):
-        res = {}
-        imgs = {}
+        res, imgs, dec, blend, evals = {}, {}, {}, {}, 0
         for half in (0, 1):
             R = render.Rasterizer(cams, api.make_config(kind, "opacity", fp16x2=half, px_per_thread=4),
                                   a.splats)
-            R.forward(sc, n_eval=False)
+            R.forward(sc, n_eval=True)
             imgs[half] = R.out.clone()
+            dec[half] = (R.n_eval.clone(), R.last.clone())
+            evals = int(R.n_eval.to(torch.int64).sum().item())
             for _ in range(3):
                 R.run_async(sc)
             res[half] = _events_ms(lambda: R.run_async(sc), max(5, a.steps // 6))
+            blend[half] = _events_ms(lambda: R.blend(n_eval=False), max(5, a.steps // 6))
             del R
         err = (imgs[1].double() - imgs[0].double()).abs()
-        mse = float((err ** 2).mean())
+        out["_cam0"][kind] = imgs[1][:a.width * a.height].view(a.height, a.width, 3).cpu().numpy()
+        f32, f16 = FLOP_PER_EVAL[kind] - HALF_FLOP_PER_EVAL[kind], HALF_FLOP_PER_EVAL[kind]
+        t_min = evals * (f32 / (p32 * 1e12) + f16 / (p16 * 1e12))
         out[kind] = {"frames_per_s_fp16x2": a.cams / (res[1] / 1e3),
                      "frames_per_s_fp32": a.cams / (res[0] / 1e3),
+                     "blend_ms_fp16x2": blend[1], "blend_ms_fp32": blend[0],
+                     "decisions_equal_fp32": bool(torch.equal(dec[0][0], dec[1][0])
+                                                  and torch.equal(dec[0][1], dec[1][1])),
+                     "roofline": {"bound": "alu", "flop_per_eval_fp32": f32, "flop_per_eval_half": f16,
+                                  "frac": t_min / (blend[1] / 1e3),
+                                  "note": "time the FFMA and HFMA2 pipes need at their measured peaks "
+                                          "for the evaluations' FP32 and half FLOPs, over the blend time"},
                      "vs_fp32": {"max": float(err.max()), "mean": float(err.mean()),
                                  "mean_per_channel": [float(v) for v in err.mean(0)],
                                  "max_per_channel": [float(v) for v in err.max(0).values],
-                                 "psnr_db": float(-10 * np.log10(max(mse, 1e-30))),
+                                 "psnr_db": float(-10 * np.log10(max(float((err ** 2).mean()), 1e-30))),
                                  "frac_px_above_2e-3": float((err.max(-1).values > 2e-3).double().mean())}}
     return out
 
@@ -786,6 +936,7 @@ def main():
         torch.cuda.set_device(local)
         _build.build()
         res = LEGS[a.leg](a)
+        res.pop("_cam0", None)
         if rank == 0:
             print(json.dumps({"leg": a.leg, "steps": a.steps, **res}), flush=True)
     elif a.impl == "reference":

@@ -17,6 +17,44 @@ static bool valid_tile(const gs_config *cfg)
     return (w == 8 || w == 16 || w == 32) && (h == 8 || h == 16 || h == 32) && w * h <= 512;
 }
 
+// A-priori bound on the rounding error of the FP16x2 alpha of render.cu
+// (alpha_pair_h2) against the FP32 alpha, per unit opacity and divided by c0,
+// i.e. as a multiple of p0 = o' c0, over Q in [0, x0]. binary16 has unit
+// roundoff u = 2^-11. The FP32 u and v^2 are rounded to half (u^2 then carries
+// 2u, v^2 u) and Q = u^2 + v^2 is one fused op (u more): |dQ| <= 3.01 u Q.
+// Horner (f1, f'2): each fused step s_k = s_{k+1} Q + p_k adds at most
+// u (|s_{k+1} Q| + |s_k|), the half coefficients u sum |p_i| Q^i, and dQ adds
+// |f'(Q)| dQ. Factored cubic: the same accounting through t1 = p3 (Q - r),
+// s = Q + f3b, q2 = s Q + f3g and alpha = t1 q2. The blend widens it by 25 %.
+static float half_alpha_bound(const CfgDev &d, int n)
+{
+    const float u = 1.f / 2048.f;
+    const float *c = d.c;
+    float worst = 0.f;
+    for (int i = 0; i <= 256; ++i) {
+        const float Q = d.x0 * (float)i / 256.f, dQ = 3.01f * u * Q;
+        float e;
+        if (n == 3 && d.f3_factored) {
+            const float t1 = c[3] * (Q - d.f3r);
+            const float dt1 = fabsf(c[3]) * dQ + u * (fabsf(c[3] * Q) + fabsf(c[3] * d.f3r) + fabsf(t1));
+            const float sq = Q + d.f3b, dsq = dQ + u * (fabsf(d.f3b) + fabsf(sq));
+            const float q2 = fmaf(sq, Q, d.f3g);
+            const float dq2 = Q * dsq + fabsf(sq) * dQ + u * (fabsf(d.f3g) + fabsf(q2));
+            e = fabsf(q2) * dt1 + fabsf(t1) * dq2 + u * fabsf(t1 * q2);
+        } else {
+            float s[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            for (int k = n; k >= 0; --k) s[k] = fmaf(Q, s[k + 1], c[k]);
+            e = 0.f;
+            for (int k = n - 1; k >= 0; --k) e += fabsf(s[k + 1] * Q) + fabsf(s[k]);
+            float qi = 1.f;
+            for (int k = 0; k <= n; ++k, qi *= Q) e += fabsf(c[k]) * qi;
+            e = e * u + fabsf(poly_deriv_eval(c, n, Q)) * dQ;
+        }
+        worst = fmaxf(worst, e);
+    }
+    return 1.25f * worst / c[0];
+}
+
 bool build_cfg(const gs_config *cfg, CfgDev *d)
 {
     if (!cfg) return false;
@@ -59,6 +97,21 @@ bool build_cfg(const gs_config *cfg, CfgDev *d)
     if (n >= 2)
         for (int i = 0; i <= 1024; ++i)
             if (poly_deriv_eval(cfg->c, n, d->x0 * i / 1024.f) > 1e-6f) d->monotone = 0;
+    // the cubic divided by (Q - x0): c3 (Q - x0)(Q^2 + f3b Q + f3g)
+    d->f3r = d->f3b = d->f3g = 0.f;
+    d->f3_factored = 0;
+    if (n == 3 && cfg->c[3] != 0.f) {
+        d->f3r = d->x0;
+        d->f3b = cfg->c[2] / cfg->c[3] + d->x0;
+        d->f3g = cfg->c[1] / cfg->c[3] + d->x0 * d->f3b;
+        // the half form needs the factors inside binary16 range
+        d->f3_factored = std::isfinite(d->f3b) && std::isfinite(d->f3g) && fabsf(d->f3b) < 3e4f &&
+                         fabsf(d->f3g) < 3e4f && fabsf(d->c[3] * d->x0) < 3e4f;
+    }
+    // exp: the half exponent p0 + p1 Q (|p0|, |p1 Q| <= -log2 eps ~ 8 where
+    // alpha >= eps/4) has error ~48 u, 1.6 % of alpha after ex2, plus ex2's own
+    // approximation and rounding; 3 % bounds both
+    d->h2_band = n ? half_alpha_bound(*d, n) : 0.03f;
     return true;
 }
 

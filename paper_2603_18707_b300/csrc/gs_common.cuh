@@ -47,6 +47,12 @@ struct CfgDev {
     int batch;
     int ppt;    // pixels per thread
     int monotone; // kernel non-increasing in Q over its support (allows skipping by Q bounds)
+    // FP16x2 blend: bound on |alpha(half) - alpha(FP32)|, as a multiple of
+    // p0 = o' c0 (polynomials) or of alpha (exp); and the cubic factored at
+    // its support root r, c3 (Q - r)(Q^2 + f3b Q + f3g), for its half form
+    float h2_band;
+    float f3r, f3b, f3g;
+    int f3_factored; // 1 when the cubic term is non-zero and the factors are finite
 };
 
 // Pointers into the record buffer (see gs_splat2d_bytes).

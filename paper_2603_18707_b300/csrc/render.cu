@@ -71,12 +71,17 @@ struct RenderArgs {
 };
 
 // FP16x2 alpha of a pixel pair (u_a, u_b computed in FP32, sharing v^2):
-// Q = u^2 + v^2 and the opacity-folded kernel in packed half2 FMAs.
+// Q = u^2 + v^2 and the opacity-folded kernel in packed half2 FMAs, before
+// the alpha_max clamp (which the caller applies in FP32: 0.99 is not a half).
 // Q is clamped to the cut x0 before f'2's polynomial so that an overflowing
-// Q (a far-away splat) gives 0 rather than inf * 0.
+// Q (a far-away splat) gives 0 rather than inf * 0. The cubic is evaluated
+// factored at its support root r, p3 (Q - r)(Q^2 + b Q + g), whose rounding
+// error stays near that of f1 (Horner's intermediates reach ~1.6 and cost
+// about twice as much); hp then holds (p3, -p3 r). The rounding error of the
+// result is bounded on the host (CfgDev::h2_band).
 template <int KIND>
 __device__ __forceinline__ float2 alpha_pair_h2(float ua, float ub, __half2 v2h, uint4 hp, __half2 x0h,
-                                                __half2 amaxh)
+                                                __half2 f3bh, __half2 f3gh, bool factored)
 {
     const __half2 p0 = *reinterpret_cast<__half2 *>(&hp.x), p1 = *reinterpret_cast<__half2 *>(&hp.y);
     const __half2 p2 = *reinterpret_cast<__half2 *>(&hp.z), p3 = *reinterpret_cast<__half2 *>(&hp.w);
@@ -90,10 +95,12 @@ __device__ __forceinline__ float2 alpha_pair_h2(float ua, float ub, __half2 v2h,
     } else if (KIND == GS_K_POLY2) {
         const __half2 Qc = __hmin2(Q, x0h);
         al = __hmul2(__hlt2(Q, x0h), __hfma2(__hfma2(p2, Qc, p1), Qc, p0));
+    } else if (factored) {
+        al = __hmul2(__hfma2(p0, Q, p1), __hfma2(__hadd2(Q, f3bh), Q, f3gh));
     } else {
         al = __hfma2(__hfma2(__hfma2(p3, Q, p2), Q, p1), Q, p0);
     }
-    return __half22float2(__hmin2(al, amaxh));
+    return __half22float2(al);
 }
 
 template <int KIND, int PPT, bool HALF>
@@ -119,7 +126,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
     const int B = cfg.batch;
 
     const float eps = cfg.eps, amax = cfg.alpha_max, tmin = cfg.t_min;
-    float T[PPT], C0[PPT], C1[PPT], C2[PPT], xs[PPT], ek[PPT];
+    float T[PPT], C0[PPT], C1[PPT], C2[PPT], xs[PPT];
     uint32_t lastc[PPT], ne[PPT];
     unsigned active = 0;
 #pragma unroll
@@ -130,17 +137,18 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
         lastc[k] = 0;
         ne[k] = n;
         if (px0 + k < cm.W && py < cm.H) active |= 1u << k;
-        // the alpha a pixel takes: eps while it is active, never once it
-        // stopped (one compare per pixel and entry instead of a mask test).
-        // FP32: a pixel that is off the frame or stopped gets x = NaN, so its
-        // Q and alpha are NaN and fail alpha >= eps (no threshold register).
-        // FP16x2 keeps a threshold: its min with alpha_max drops a NaN.
-        ek[k] = (active >> k & 1u) ? eps : INFINITY;
-        if (!HALF && !(active >> k & 1u)) xs[k] = NAN;
+        // a pixel that is off the frame or has stopped gets x = NaN: its Q
+        // and alpha are NaN (in FP32 and in half) and fail every alpha
+        // compare, so no per-pixel mask test is needed
+        if (!(active >> k & 1u)) xs[k] = NAN;
     }
-    const __half2 x0h = __float2half2_rn(fminf(cfg.x0, 60000.f)), amaxh = __float2half2_rn(amax);
-    // the FP16x2 alphas carry ~1e-3 absolute error: skip only far below eps
-    const float eps_skip = HALF ? 0.5f * eps : eps * (1.f - 1.f / 1024.f);
+    const __half2 x0h = __float2half2_rn(fminf(cfg.x0, 60000.f));
+    const __half2 f3bh = __float2half2_rn(cfg.f3b), f3gh = __float2half2_rn(cfg.f3g);
+    const bool factored = KIND == GS_K_POLY3 && cfg.f3_factored;
+    // skip threshold of the per-run test: just below eps, so that rounding
+    // never skips an entry a pixel takes (the FP16x2 path takes the FP32
+    // path's decisions, so the same test serves both)
+    const float eps_skip = eps * (1.f - 1.f / 1024.f);
     for (uint32_t base = 0; base < n; base += B) {
         if (__syncthreads_count(active != 0) == 0) break;
         for (int i = threadIdx.x; i < B; i += nthreads) {
@@ -153,8 +161,12 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                 s_b[i] = k.b;
                 s_c[i] = k.c;
                 if (HALF) {
-                    const __half2 h[4] = {__float2half2_rn(k.b.y), __float2half2_rn(k.b.z),
-                                          __float2half2_rn(k.b.w), __float2half2_rn(k.c.w)};
+                    __half2 h[4] = {__float2half2_rn(k.b.y), __float2half2_rn(k.b.z),
+                                    __float2half2_rn(k.b.w), __float2half2_rn(k.c.w)};
+                    if (factored) {
+                        h[0] = __float2half2_rn(k.c.w);
+                        h[1] = __float2half2_rn(-k.c.w * cfg.f3r);
+                    }
                     s_h[i] = *reinterpret_cast<const uint4 *>(h);
                 }
             }
@@ -192,33 +204,71 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                     if (alpha_of_q<KIND>(cfg, b, p3, fmaf(um, um, v2)) < eps_skip) continue;
                 }
             }
-            float al[PPT];
-            if (HALF) {
+            const float4 col = s_c[j];
+            const uint32_t pos = base + j + 1;
+            if constexpr (HALF) {
+                // alphas in packed half, decisions as the FP32 path takes them:
+                // d bounds |alpha(half) - alpha(FP32)| for this entry, so an
+                // alpha further than d from eps is on the FP32 alpha's side of
+                // it; within d (rare) the pixel's alpha is recomputed with the
+                // FP32 path's arithmetic, and so is it where T (1 - alpha) lies
+                // within T d of t_min (the stop decision)
                 const uint4 hp = s_h[j];
                 const __half2 v2h = __float2half2_rn(v2);
+                float al[PPT];
 #pragma unroll
                 for (int k = 0; k < PPT; k += 2) {
-                    const float2 ap = alpha_pair_h2<KIND>(fmaf(a.x, xs[k], ub), fmaf(a.x, xs[k + 1], ub),
-                                                          v2h, hp, x0h, amaxh);
+                    const float2 ap = alpha_pair_h2<KIND>(fmaf(a.x, xs[k], ub), fmaf(a.x, xs[k + 1], ub), v2h, hp,
+                                                          x0h, f3bh, f3gh, factored);
                     al[k] = ap.x;
                     al[k + 1] = ap.y;
                 }
-            } else {
+                const float d = cfg.h2_band * (KIND == GS_K_EXP ? eps : b.y);
+                const float lo = eps - d, hi = eps + d;
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    // min(alpha_max, x) < eps exactly when x < eps: the clamp
-                    // is applied only to entries that are blended
-                    const float u = fmaf(a.x, xs[k], ub);
-                    const float Q = fmaf(u, u, v2);
-                    al[k] = alpha_of_q<KIND>(cfg, b, p3, Q);
+                    float x = al[k];
+                    if (!(x >= lo)) continue; // below eps for certain, or the pixel stopped (NaN)
+                    if (x < hi) {
+                        const float u = fmaf(a.x, xs[k], ub);
+                        x = alpha_of_q<KIND>(cfg, b, p3, fmaf(u, u, v2));
+                        if (!(x >= eps)) continue;
+                    }
+                    x = fminf(amax, x);
+                    float Tn = fmaf(-x, T[k], T[k]);
+                    if (Tn < fmaf(T[k], KIND == GS_K_EXP ? cfg.h2_band * x : d, tmin)) {
+                        // (recomputing an alpha that is already FP32 gives the same value)
+                        const float u = fmaf(a.x, xs[k], ub);
+                        x = fminf(amax, alpha_of_q<KIND>(cfg, b, p3, fmaf(u, u, v2)));
+                        Tn = fmaf(-x, T[k], T[k]);
+                    }
+                    if (Tn < tmin) {
+                        active &= ~(1u << k);
+                        xs[k] = NAN;
+                        ne[k] = pos;
+                        continue;
+                    }
+                    const float w = x * T[k];
+                    C0[k] = fmaf(col.x, w, C0[k]);
+                    C1[k] = fmaf(col.y, w, C1[k]);
+                    C2[k] = fmaf(col.z, w, C2[k]);
+                    T[k] = Tn;
+                    lastc[k] = pos;
                 }
+            } else {
+            float al[PPT];
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                // min(alpha_max, x) < eps exactly when x < eps: the clamp
+                // is applied only to entries that are blended
+                const float u = fmaf(a.x, xs[k], ub);
+                const float Q = fmaf(u, u, v2);
+                al[k] = alpha_of_q<KIND>(cfg, b, p3, Q);
             }
-            const float4 col = s_c[j];
-            const uint32_t pos = base + j + 1;
             if constexpr (blend_branchless<KIND>()) {
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    const bool use = al[k] >= (HALF ? ek[k] : eps);
+                    const bool use = al[k] >= eps;
                     const float a = fminf(amax, al[k]);
                     const float Tn = fmaf(-a, T[k], T[k]);
                     const bool stop = use && Tn < tmin;
@@ -231,23 +281,17 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                     lastc[k] = add ? pos : lastc[k];
                     ne[k] = stop ? pos : ne[k];
                     active &= ~((unsigned)stop << k);
-                    if (HALF)
-                        ek[k] = stop ? INFINITY : ek[k];
-                    else
-                        xs[k] = stop ? NAN : xs[k];
+                    xs[k] = stop ? NAN : xs[k];
                 }
             } else {
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
-                    if (!(al[k] >= (HALF ? ek[k] : eps))) continue;
+                    if (!(al[k] >= eps)) continue;
                     al[k] = fminf(amax, al[k]);
                     const float Tn = fmaf(-al[k], T[k], T[k]);
                     if (Tn < tmin) {
                         active &= ~(1u << k);
-                        if (HALF)
-                            ek[k] = INFINITY;
-                        else
-                            xs[k] = NAN;
+                        xs[k] = NAN;
                         ne[k] = pos;
                         continue;
                     }
@@ -258,6 +302,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                     T[k] = Tn;
                     lastc[k] = pos;
                 }
+            }
             }
         }
     }

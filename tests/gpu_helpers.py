@@ -64,3 +64,36 @@ def expected_binning(rec: dict, cams, tile_w: int, tile_h: int, P: int):
         ranges[T[starts], 0] = starts
         ranges[T[starts], 1] = ends
     return I, keys, ranges.ravel()
+
+
+def oracle_tile_list(o: dict, tile: int, tiles_x: int) -> np.ndarray:
+    """Splat ids of the oracle's list for one tile, from the oracle's own
+    projection records (splats_to_numpy): drawn splats whose rectangle
+    contains the tile, in (depth, index) order."""
+    tx, ty = tile % tiles_x, tile // tiles_x
+    r = o["rect"]
+    m = ((o["visible"] == 1) & (o["tiles"] > 0) & (r[:, 0] <= tx) & (r[:, 2] >= tx)
+         & (r[:, 1] <= ty) & (r[:, 3] >= ty))
+    ids = np.nonzero(m)[0]
+    return ids[np.lexsort((ids, o["depth"][ids]))]
+
+
+def n_eval_mismatches(nev_gpu: np.ndarray, nev_orc: np.ndarray, far: np.ndarray, O: np.ndarray,
+                      G: np.ndarray) -> int:
+    """Pixels of one tile (flattened arrays) whose GPU evaluation count is
+    not the oracle's. The GPU's FP32 rectangles are conservative, so its list
+    G may hold entries the oracle's list O lacks (all below eps at every pixel
+    centre); a pixel that stops on O[e - 1] must stop on that same splat in G,
+    and one that never stops evaluates all of G. With e == len(O) the oracle
+    either stopped on its last entry or never stopped: both are accepted.
+    Only pixels away from threshold flips (far) are compared."""
+    pos = {int(s): k for k, s in enumerate(G.tolist())}
+    bad = 0
+    for p in np.nonzero(far)[0]:
+        e, g = int(nev_orc[p]), int(nev_gpu[p])
+        if e < O.size:
+            ok = g == pos.get(int(O[e - 1]), -2) + 1
+        else:
+            ok = g == G.size or (O.size > 0 and g == pos.get(int(O[-1]), -2) + 1)
+        bad += not ok
+    return bad

@@ -278,3 +278,63 @@ def test_differentiable_1M_scene_sampled_tiles(gs, orc):
     gpu, _ = _gpu_grads(api, render, raw, [cam], "poly1", "opacity", w, (0.0, 0.0, 0.0))
     ref = orc.render_backward(sc, oc, cfg, w, (0.0, 0.0, 0.0))
     _check(gpu, ref)
+
+
+def test_backward_finite_differences_256_splats_64x64(gs, orc):
+    """The finite-difference sub-case of the differentiable workload: 256
+    splats (SH degree 3) at 64x64, f1 with opacity culling. GPU gradients
+    against FP64 central differences of the oracle's forward, on 60 sampled
+    entries of each parameter tensor where no skip / clamp / stop decision
+    flips. Each entry whose gradient is not negligible (|fd| >= 1% of the
+    tensor's largest) must agree within 1e-3 relative; the near-zero rest
+    within 1e-5 of the largest (FP32 accumulation over many pixels leaves an
+    absolute error of that order, which is no relative bound for a
+    near-zero gradient)."""
+    import json
+    import os
+    api, render, synth = gs
+    raw = _small_scene(P=256, seed=11)
+    cam = synth.look_at([0.3, -0.2, -2.5], [0, 0, 0], 64, 64, 60.0)
+    oc = orc.camera_from_dict(cam)
+    sc = _oracle_inputs(orc, raw)
+    cfg = orc.make_config("poly1", KIND_COEFFS["poly1"], "opacity")
+    bg = (0.1, 0.1, 0.1)
+    w = _masked_weights(orc, sc, oc, "poly1", (64, 64, 3), seed=5)
+    gpu, _ = _gpu_grads(api, render, raw, [cam], "poly1", "opacity", w, bg)
+    base = orc.decisions(sc, oc, cfg)
+    rng = np.random.default_rng(2)
+    stats, checked = {}, 0
+    for name in ("means", "scales", "quats", "opacities", "sh"):
+        arr = sc[name]
+        flat = list(np.ndindex(arr.shape))
+        pairs = []
+        for idx in [flat[i] for i in rng.choice(len(flat), min(60, len(flat)), replace=False)]:
+            h = 1e-6 * max(1.0, abs(arr[idx]))
+            vals = []
+            for sgn in (1, -1):
+                s2 = {k: (np.array(v, copy=True) if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
+                s2[name][idx] += sgn * h
+                if not np.array_equal(orc.decisions(s2, oc, cfg), base):
+                    break
+                img, _, _ = orc.render_untiled(s2, oc, cfg, bg)
+                vals.append((img * w).sum())
+            if len(vals) == 2:
+                pairs.append((gpu[name][idx], (vals[0] - vals[1]) / (2 * h)))
+        g, fd = np.array(pairs).T
+        big = np.abs(fd).max()
+        sig = np.abs(fd) >= 0.01 * big
+        rel = np.abs(g - fd)[sig] / np.abs(fd)[sig]
+        small = np.abs(g - fd)[~sig] / big
+        stats[name] = {"checked": int(g.size), "significant": int(sig.sum()),
+                       "max_rel_significant": float(rel.max(initial=0.0)),
+                       "max_abs_small_over_largest": float(small.max(initial=0.0))}
+        assert sig.sum() >= 10, name
+        assert rel.max() <= 1e-3, (name, stats[name])
+        assert small.max(initial=0.0) <= 1e-5, (name, stats[name])
+        checked += g.size
+    rep = os.environ.get("GS_REPORT_DIR")
+    if rep:
+        os.makedirs(rep, exist_ok=True)
+        with open(os.path.join(rep, "fd_256_64x64.json"), "w") as f:
+            json.dump(stats, f, indent=1)
+    assert checked >= 250

@@ -297,3 +297,71 @@ def test_gather_rows_and_reordered_scene_renders_the_same(gs):
     u2, _ = render.spatial_order(u)
     x, y = both(u, u2, 100_000)
     assert torch.equal(x, y)
+
+
+def test_persistent_graph_mixed_batch_matches_oracle(gs, orc):
+    """The serving launch against the FP64 oracle: cameras of all four
+    resolutions of the mixed workload (one full 3840x2160 frame among them),
+    the blend as one persistent launch, the whole pass replayed from a CUDA
+    graph, with the launch shape the autotuner picks here and with the 32x16
+    tiles / 4 pixels per thread it picks on the 6M-splat batch. Sampled tiles
+    of every camera (the last, ragged tile included): pixels within 2e-4 of
+    the oracle's tile render of the same tile shape outside threshold flips,
+    and evaluation counts equal to the oracle's (same stopping splat)."""
+    api, render, synth = gs
+    from gpu_helpers import (KIND_COEFFS, NEAR_MARGIN, TOL_FP32, n_eval_mismatches,
+                             oracle_tile_list)
+    from paper_2603_18707_b300 import autotune
+    P = 600_000
+    raw = synth.scene_clusters(P, 4, sh_degree=3)
+    sc = render.activate(raw)
+    cams = synth.mixed_cameras(10)  # 4 x 640x360, 3 x 1280x720, 2 x 1920x1080, 1 x 3840x2160
+    assert sorted({(c["width"], c["height"]) for c in cams}) == [(640, 360), (1280, 720), (1920, 1080),
+                                                                   (3840, 2160)]
+    tuned = autotune.autotune(cams, "poly1", "opacity", sc, P, persistent=True, steps=2, cache=None)
+    shapes = [autotune.config_overrides(tuned), {"tile": (32, 16), "batch": 256, "px_per_thread": 4}]
+    osc = orc.activate(raw)
+    rng = np.random.default_rng(3)
+    checked = 0
+    for over in shapes:
+        cfg = api.make_config("poly1", "opacity", **over)
+        R = render.Rasterizer(cams, cfg, P, persistent=True)
+        R.forward(sc)
+        graph = R.capture(sc, n_eval=True)
+        R.out.zero_()
+        R.n_eval.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        imgs = [im.cpu().numpy() for im in R.images()]
+        nevs = [n.cpu().numpy().astype(np.int64) for n in R.per_camera(R.n_eval)]
+        vals, rg = R.vals.cpu().numpy().astype(np.int64), R.ranges.cpu().numpy().reshape(-1, 2)
+        tw, th = over["tile"]
+        ocfg = orc.make_config("poly1", KIND_COEFFS["poly1"], "opacity", tile=(tw, th))
+        base = 0
+        for c, (cam, img, nev_g) in enumerate(zip(cams, imgs, nevs)):
+            W, H = cam["width"], cam["height"]
+            tx, ty = -(-W // tw), -(-H // th)
+            tiles = sorted(set(rng.integers(0, tx * ty, 5).tolist()) | {tx * ty - 1})
+            oc = orc.camera_from_dict(cam)
+            s2d = orc.project(osc, oc, ocfg)
+            ref, _, _, nev_o, _, _ = orc.render_tiled(osc, oc, ocfg, tiles=tiles, s2d=s2d)
+            # decision margins over the universal-cull lists, which contain every
+            # entry the GPU's conservative rectangles can add
+            ucfg = orc.make_config("poly1", KIND_COEFFS["poly1"], "universal", tile=(tw, th))
+            *_, margin = orc.render_tiled(osc, oc, ucfg, tiles=tiles, with_margin=True)
+            o = orc.splats_to_numpy(s2d, P)
+            for t in tiles:
+                y0, x0 = (t // tx) * th, (t % tx) * tw
+                ys, xs = slice(y0, min(y0 + th, H)), slice(x0, min(x0 + tw, W))
+                far = margin[ys, xs] >= NEAR_MARGIN
+                err = np.abs(img[ys, xs].astype(np.float64) - ref[ys, xs]).max(-1)
+                assert err[far].max(initial=0.0) < TOL_FP32, (c, t, over)
+                assert (~far).sum() <= 0.05 * far.size + 2
+                G = vals[rg[base + t, 0]:rg[base + t, 1]] - c * P
+                O = oracle_tile_list(o, t, tx)
+                assert set(O.tolist()) <= set(G.tolist())
+                assert n_eval_mismatches(nev_g[ys, xs].ravel(), nev_o[ys, xs].ravel(), far.ravel(), O, G) == 0
+                checked += 1
+            base += tx * ty
+        del graph, R
+    assert checked >= 2 * 10 * 2

@@ -5,7 +5,8 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_helpers import (KIND_COEFFS, NEAR_MARGIN, TOL_FP32, expected_binning, parse_splat2d)
+from gpu_helpers import (KIND_COEFFS, NEAR_MARGIN, TOL_FP32, expected_binning, n_eval_mismatches,
+                         oracle_tile_list, parse_splat2d)
 
 pytestmark = pytest.mark.gpu
 
@@ -259,13 +260,47 @@ def test_tile_shapes_and_pixels_per_thread(gs, orc, small):
     oc = orc.camera_from_dict(cam)
     ref, _, _ = orc.render_untiled(sc, oc, _oracle_cfg(orc, "poly1", "opacity"))
     *_, margin = orc.render_tiled(sc, oc, _oracle_cfg(orc, "poly1", "universal"), with_margin=True)
-    for tile, ppts in (((16, 16), (1, 2, 4)), ((8, 8), (1, 2, 4)), ((32, 8), (1, 4)), ((8, 16), (1, 2))):
+    for tile, ppts in (((16, 16), (1, 2, 4)), ((8, 8), (1, 2, 4)), ((32, 8), (1, 4)), ((8, 16), (1, 2)),
+                       ((32, 16), (2, 4)), ((16, 32), (2, 4))):
         imgs = [_gpu(gs, small, [cam], "poly1", "opacity", tile=tile, px_per_thread=p).images()[0]
                 .cpu().numpy() for p in ppts]
         for im in imgs[1:]:
             assert np.array_equal(im, imgs[0]), tile
         worst, _, _ = _compare(imgs[0], ref, margin)
         assert worst < TOL_FP32, tile
+
+
+@pytest.mark.parametrize("kind,cull", [("poly1", "opacity"), ("exp", "opacity"), ("poly3", "universal")])
+def test_n_eval_matches_oracle_count(gs, orc, small, kind, cull):
+    """The per-pixel evaluation count (the numerator of Gsplat-evals/s): the
+    list position where the pixel stops, or the list length. It equals the
+    oracle's tile-binned count on every pixel away from threshold flips,
+    once the GPU's conservative extra entries are accounted for (the pixel
+    stops on the same splat)."""
+    from paper_2603_18707_b300 import synth
+    cam = synth.camera_small()
+    R = _gpu(gs, small, [cam], kind, cull)
+    nev_g = R.per_camera(R.n_eval)[0].cpu().numpy().astype(np.int64)
+    vals, rg = R.vals.cpu().numpy().astype(np.int64), R.ranges.cpu().numpy().reshape(-1, 2)
+    sc, oc, cfg = orc.activate(small), orc.camera_from_dict(cam), _oracle_cfg(orc, kind, cull)
+    s2d = orc.project(sc, oc, cfg)
+    o = orc.splats_to_numpy(s2d, R.P)
+    _, _, _, nev_o, llen, margin = orc.render_tiled(sc, oc, cfg, s2d=s2d, with_margin=True)
+    tiles_x = 8
+    bad, total_g, total_o = 0, 0, 0
+    for t in range(64):
+        ys, xs = slice((t // tiles_x) * 16, (t // tiles_x) * 16 + 16), slice((t % tiles_x) * 16,
+                                                                            (t % tiles_x) * 16 + 16)
+        G = vals[rg[t, 0]:rg[t, 1]]
+        O = oracle_tile_list(o, t, tiles_x)
+        assert O.size == llen[t]
+        assert set(O.tolist()) <= set(G.tolist())  # conservative lists
+        far = (margin[ys, xs] >= NEAR_MARGIN).ravel()
+        bad += n_eval_mismatches(nev_g[ys, xs].ravel(), nev_o[ys, xs].ravel(), far, O, G)
+        total_g += int(nev_g[ys, xs].sum())
+        total_o += int(nev_o[ys, xs].sum())
+    assert bad == 0
+    assert total_o <= total_g <= total_o * 1.01  # extras are below 1% of the evaluations
 
 
 def test_edge_cases(gs, orc):
@@ -360,14 +395,16 @@ def test_full_size_scene_sampled_tiles(gs, orc):
     cams = synth.orbit_cameras(16, 1920, 1080)
     R = _gpu(gs, raw, cams, "poly1", "opacity", keep_keys=False)
     img = R.images()[0].cpu().numpy()
+    nev_g = R.per_camera(R.n_eval)[0].cpu().numpy().astype(np.int64)
     oc = orc.camera_from_dict(cams[0])
     cfg = _oracle_cfg(orc, "poly1", "opacity")
     tx, ty = (1920 + 15) // 16, (1080 + 15) // 16
     rng = np.random.default_rng(0)
     tiles = sorted(set(rng.integers(0, tx * ty, 20).tolist()) |
                    {0, tx - 1, (ty - 1) * tx, tx * ty - 1})
-    ref, _, _, nev, _, margin = orc.render_tiled(orc.activate(raw), oc, cfg, tiles=tiles,
-                                                 with_margin=True)
+    sc = orc.activate(raw)
+    s2d = orc.project(sc, oc, cfg)
+    ref, _, _, nev, _, margin = orc.render_tiled(sc, oc, cfg, tiles=tiles, s2d=s2d, with_margin=True)
     mask = np.zeros((1080, 1920), bool)
     for t in tiles:
         y, x = (t // tx) * 16, (t % tx) * 16
@@ -376,6 +413,17 @@ def test_full_size_scene_sampled_tiles(gs, orc):
     near = margin < NEAR_MARGIN
     assert err[mask & ~near].max() < TOL_FP32
     assert (mask & near).sum() < 0.02 * mask.sum()
+    # evaluation counts (camera 0's records are ids 0 .. P-1, its tiles 0 .. tx*ty-1)
+    o = orc.splats_to_numpy(s2d, R.P)
+    vals, rg = R.vals.cpu().numpy().astype(np.int64), R.ranges.cpu().numpy().reshape(-1, 2)
+    bad = 0
+    for t in tiles:
+        y, x = (t // tx) * 16, (t % tx) * 16
+        G, O = vals[rg[t, 0]:rg[t, 1]], oracle_tile_list(o, t, tx)
+        assert set(O.tolist()) <= set(G.tolist())
+        far = ~near[y:y + 16, x:x + 16].ravel()
+        bad += n_eval_mismatches(nev_g[y:y + 16, x:x + 16].ravel(), nev[y:y + 16, x:x + 16].ravel(), far, O, G)
+    assert bad == 0
 
 
 @pytest.mark.parametrize("kind,cull", [("poly1", "opacity"), ("exp", "opacity"), ("poly3", "universal")])

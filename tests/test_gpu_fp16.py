@@ -1,7 +1,12 @@
 """Precision variant: quadric and polynomial in packed FP16x2 FMAs, colour and
-transmittance in FP32. Errors against the FP64 oracle and the FP32 GPU path
-are measured and reported (max / mean per channel, PSNR, and the share of
-pixels above the 2e-3 bound)."""
+transmittance in FP32. Each entry's half alpha carries a bound on its rounding
+error; within that bound of eps (or of the t_min stop) the pixel decides in
+FP32, so the variant takes the FP32 path's skip decisions, and its stop
+decisions too except where its transmittance (which carries the rounding of
+earlier half alphas) lies within that drift of t_min. Against the FP64 oracle
+every channel of every pixel away from threshold flips (the FP32 path's
+definition) lies within 2e-3; max / mean per channel, PSNR and the share of
+pixels above 2e-3 are reported."""
 import json
 import os
 
@@ -41,6 +46,20 @@ def _stats(img, ref, margin=None):
     return out
 
 
+def _check_against_fp32(imgs, dec, name):
+    """Decisions (evaluation count and last contributor per pixel) equal the
+    FP32 path's on all but a few stop decisions near t_min, and wherever they
+    are equal the images differ only by the half alphas' rounding: within
+    2e-3 over the whole frame."""
+    same = ((dec[1][0] == dec[0][0]) & (dec[1][1] == dec[0][1])).cpu().numpy()
+    err = np.abs(imgs[1].astype(np.float64) - imgs[0]).reshape(-1, 3).max(-1)
+    _report(name + "-decisions", {"vs_fp32_decisions": {"pixels_differing": int((~same).sum()),
+                                                        "max_where_same": float(err[same].max(initial=0.0)),
+                                                        "max_where_differing": float(err[~same].max(initial=0.0))}})
+    assert (~same).mean() < 1e-3
+    assert err[same].max(initial=0.0) <= TOL_FP16
+
+
 def _report(name, d):
     if not REPORT:
         return
@@ -55,11 +74,12 @@ def test_fp16x2_small_scene_against_oracle(gs, orc, kind):
     raw = synth.scene_uniform(4096, 0)
     cam = synth.camera_small()
     sc = render.activate(raw)
-    imgs = {}
+    imgs, dec = {}, {}
     for half in (0, 1):
         R = render.Rasterizer([cam], api.make_config(kind, "opacity", fp16x2=half, px_per_thread=2), 4096)
         R.forward(sc)
         imgs[half] = R.images()[0].cpu().numpy()
+        dec[half] = (R.n_eval.clone(), R.last.clone())  # the skip / stop decisions
     oc = orc.camera_from_dict(cam)
     osc = orc.activate(raw)
     ref, _, _ = orc.render_untiled(osc, oc, orc.make_config(kind, KIND_COEFFS[kind], "opacity"))
@@ -68,25 +88,29 @@ def test_fp16x2_small_scene_against_oracle(gs, orc, kind):
     s_orc = _stats(imgs[1], ref, margin)
     s_fp32 = _stats(imgs[1], imgs[0].astype(np.float64))
     _report(f"small-{kind}", {"vs_oracle": s_orc, "vs_fp32": s_fp32})
+    assert s_orc["max_outside_threshold_flips"] <= TOL_FP16, s_orc
+    assert (margin < NEAR_MARGIN).mean() < 0.01
     assert s_orc["mean"] < 2e-4
-    assert s_orc["frac_px_above_2e-3"] < 0.01
     assert s_orc["psnr_db"] > 55
+    _check_against_fp32(imgs, dec, f"small-{kind}")
 
 
-@pytest.mark.parametrize("kind", ["poly1", "poly2"])
+@pytest.mark.parametrize("kind", ["poly1", "poly2", "poly3", "exp"])
 def test_fp16x2_full_scene_sampled_tiles(gs, orc, kind):
-    """3M-splat 1920x1080 scene, camera 0: FP16x2 vs FP32 GPU over the whole
-    frame, and vs the FP64 oracle on 24 sampled tiles."""
+    """3M-splat 1920x1080 scene, camera 0, in the launch configuration of the
+    benchmark (4 pixels per thread): FP16x2 vs FP32 GPU over the whole frame
+    (identical decisions), and vs the FP64 oracle on 24 sampled tiles."""
     api, render, synth = gs
     raw = synth.scene_clusters(3_000_000, 0, sh_degree=3)
     cam = synth.orbit_cameras(16, 1920, 1080)[0]
     sc = render.activate(raw)
-    imgs = {}
+    imgs, dec = {}, {}
     for half in (0, 1):
-        R = render.Rasterizer([cam], api.make_config(kind, "opacity", fp16x2=half, px_per_thread=2),
+        R = render.Rasterizer([cam], api.make_config(kind, "opacity", fp16x2=half, px_per_thread=4),
                               3_000_000)
         R.forward(sc)
         imgs[half] = R.images()[0].cpu().numpy()
+        dec[half] = (R.n_eval.clone(), R.last.clone())
         del R
     oc = orc.camera_from_dict(cam)
     tx, ty = 120, 68
@@ -102,8 +126,10 @@ def test_fp16x2_full_scene_sampled_tiles(gs, orc, kind):
     s_orc = _stats(imgs[1][mask], ref[mask], margin[mask])
     s_fp32 = _stats(imgs[1], imgs[0].astype(np.float64))
     _report(f"3M-1080p-{kind}", {"vs_oracle_sampled_tiles": s_orc, "vs_fp32_full_frame": s_fp32})
+    assert s_orc["max_outside_threshold_flips"] <= TOL_FP16, s_orc
+    assert (margin[mask] < NEAR_MARGIN).mean() < 0.05  # flips are a small minority
     assert s_orc["mean"] < 2e-4 and s_fp32["mean"] < 2e-4
-    assert s_orc["frac_px_above_2e-3"] < 0.01 and s_fp32["frac_px_above_2e-3"] < 0.01
+    _check_against_fp32(imgs, dec, f"3M-1080p-{kind}")
 
 
 def test_fp16x2_persistent_and_backward_refusal(gs):
