@@ -864,16 +864,20 @@ def bench_f2_range(a):
 
 def bench_tensor_quadric(a):
     """Sec. 5.1 mapped onto the tensor cores, on the headline workload: the
-    quadric of every (pixel, splat) pair of a batch by mma.sync TF32 with
-    split weights (config tensor_alpha), against the FP32 blend: frames/s
-    and the largest per-channel difference of the images."""
+    quadric of every (pixel, splat) pair of a batch with split TF32 weights,
+    by warp-level mma.sync (config tensor_alpha = 1) and by tcgen05.mma into
+    TMEM (tensor_alpha = 2), against the FP32 blend: frames/s, blend time and
+    the largest per-channel difference of the images."""
+    import torch
+
     from paper_2603_18707_b300 import api, render, synth
     raw, sc, _, _ = load_scene(a, a.splats)
     cams = synth.orbit_cameras(a.cams, a.width, a.height)
     out = {}
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
     for kind in ("poly1", "exp"):
         res, imgs, blend = {}, {}, {}
-        for tc in (0, 1):
+        for tc in (0, 1, 2):
             R = render.Rasterizer(cams, api.make_config(kind, "opacity", tensor_alpha=tc), a.splats)
             R.forward(sc, n_eval=False)
             imgs[tc] = R.out.clone()
@@ -882,9 +886,14 @@ def bench_tensor_quadric(a):
             res[tc] = _events_ms(lambda: R.run_async(sc), max(5, a.steps // 6))
             blend[tc] = _events_ms(lambda: R.blend(n_eval=False), max(5, a.steps // 6))
             del R
-        out[kind] = {"frames_per_s_tensor": a.cams / (res[1] / 1e3), "frames_per_s_fp32": a.cams / (res[0] / 1e3),
-                     "blend_ms_tensor": blend[1], "blend_ms_fp32": blend[0],
-                     "max_abs_diff_vs_fp32": float((imgs[1] - imgs[0]).abs().max())}
+        api.gs_render_status_async(st)
+        out[kind] = {"frames_per_s_fp32": a.cams / (res[0] / 1e3),
+                     "frames_per_s_mma_sync": a.cams / (res[1] / 1e3),
+                     "frames_per_s_tcgen05": a.cams / (res[2] / 1e3),
+                     "blend_ms_fp32": blend[0], "blend_ms_mma_sync": blend[1], "blend_ms_tcgen05": blend[2],
+                     "max_abs_diff_vs_fp32_mma_sync": float((imgs[1] - imgs[0]).abs().max()),
+                     "max_abs_diff_vs_fp32_tcgen05": float((imgs[2] - imgs[0]).abs().max()),
+                     "device_error_word": int(st.item())}
     return out
 
 

@@ -113,10 +113,13 @@ typedef struct {
     int32_t batch;        /* splats staged in shared memory per round: 32..256 */
     int32_t px_per_thread;/* pixels per thread in the blend: 1, 2 or 4 */
     int32_t fp16x2;       /* 1: quadric and polynomial in packed FP16x2 */
-    int32_t tensor_alpha; /* 1: quadric of every (pixel, splat) pair on the tensor cores
-                             (mma.sync TF32, weights split in two TF32 parts); needs
-                             16x16 tiles, fp16x2 = 0 and the one-CTA-per-tile launch;
-                             forward only (gs_render_backward: GS_ERR_UNSUPPORTED) */
+    int32_t tensor_alpha; /* quadric of every (pixel, splat) pair on the tensor cores
+                             (Sec. 5.1), weights split in two TF32 parts: 1 warp-level
+                             mma.sync TF32 (32 splats per batch); 2 tcgen05.mma
+                             kind::tf32 into TMEM (64 splats per batch, M = 128).
+                             Needs 16x16 tiles, fp16x2 = 0 and the one-CTA-per-tile
+                             launch; forward only (gs_render_backward:
+                             GS_ERR_UNSUPPORTED) */
     int32_t reserved[3];
 } gs_config;
 
@@ -204,6 +207,14 @@ gs_status gs_render(void *stream, const gs_camera *cams, int32_t ncam, int32_t P
                     const uint32_t *d_ranges, const float *bg, float *d_out_rgb,
                     float *d_final_T, uint32_t *d_last, uint32_t *d_n_eval, void *d_work);
 
+/* Device error word of the blend: GS_ERR_TIMEOUT when a bounded wait of the
+ * tcgen05 tensor-core variant (tensor_alpha = 2) gave up (its tiles are then
+ * incomplete). One word per device, shared by every gs_render call of the
+ * process: enqueues on `stream` a copy of it to dst (uint32, device or pinned
+ * host memory) and clears it. GS_ERR_ARG for a null dst, GS_ERR_CUDA if a copy
+ * cannot be enqueued. */
+gs_status gs_render_status_async(void *stream, uint32_t *dst);
+
 /* Reverse pass of gs_render and gs_preprocess for one or more cameras:
  * gradients of a loss L with respect to the splat inputs, given
  * dL/d(out_rgb). Needs the forward's d_final_T and d_last. Output gradient
@@ -273,14 +284,16 @@ gs_status gs_workspace_status(void *stream, void *d_workspace, int32_t *code);
 gs_status gs_workspace_status_async(void *stream, void *d_workspace, uint32_t *dst);
 
 /* Self-test of the bounded waits (failure detection without a fault; not
- * part of the rendering path). Runs one of the two decoupled look-back
- * routines of gs_bin_sort against a predecessor partition that never
- * publishes its count: which = 0 the scalar look-back (compaction, emission),
- * which = 1 the per-digit look-back of a radix pass. The wait gives up after
- * spin_limit short sleeps and ORs GS_ERR_TIMEOUT into the error word
+ * part of the rendering path). Runs one of the bounded waits against an
+ * event that never comes: which = 0 the scalar decoupled look-back of
+ * gs_bin_sort (compaction, emission) against a predecessor partition that
+ * never publishes its count; which = 1 the per-digit look-back of a radix
+ * pass; which = 2 the mbarrier wait of the tcgen05 blend on a barrier that
+ * no arrival completes. The wait gives up after spin_limit polls (short
+ * sleeps for the look-backs) and ORs GS_ERR_TIMEOUT into the error word
  * d_scratch[0]; the launch returns and the context stays usable.
  * d_scratch: GS_SELFTEST_SCRATCH_BYTES of device memory (4-byte aligned),
- * cleared by the call. Returns GS_ERR_ARG for a null pointer, which not 0/1,
+ * cleared by the call. Returns GS_ERR_ARG for a null pointer, which not 0/1/2,
  * or spin_limit outside [1, 2^20]. */
 #define GS_SELFTEST_SCRATCH_BYTES 4096
 gs_status gs_selftest_lookback_timeout(void *stream, int32_t which, uint32_t *d_scratch, int32_t spin_limit);

@@ -68,6 +68,7 @@ _SIGS = {
                                   _vp]),
     "gs_workspace_status": (_i32, [_vp, _vp, C.POINTER(_i32)]),
     "gs_workspace_status_async": (_i32, [_vp, _vp, _vp]),
+    "gs_render_status_async": (_i32, [_vp, _vp]),
     "gs_spatial_order_workspace_bytes": (_sz, [_i32]),
     "gs_spatial_order": (_i32, [_vp, _i32, _vp, _vp, _vp]),
     "gs_gather_rows": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp]),

@@ -179,6 +179,13 @@ def gs_workspace_status_async(workspace, dst, stream=None) -> None:
                                                                        _p(dst)))
 
 
+def gs_render_status_async(dst, stream=None) -> None:
+    """Enqueues a copy of the blend's device error word (GS_ERR_TIMEOUT when
+    a wait of the tcgen05 variant gave up) into dst (a 4-byte device or
+    pinned host tensor) and clears it."""
+    check("gs_render_status_async", lib().gs_render_status_async(_stream(stream), _p(dst)))
+
+
 def gs_spatial_order(means, stream=None):
     """Z-order permutation of the splats (int32 tensor [P]; see gs.h):
     store a scene in this order once when it is loaded."""

@@ -30,7 +30,7 @@
 #include <algorithm>
 #include <utility>
 
-#include "gs_common.cuh"
+#include "blend_math.cuh"
 
 namespace gs {
 namespace {
@@ -992,10 +992,19 @@ __global__ void lookback_selftest_kernel(int which, uint32_t *state, uint32_t *e
 extern "C" gs_status gs_selftest_lookback_timeout(void *stream, int32_t which, uint32_t *d_scratch,
                                                   int32_t spin_limit)
 {
-    if (!d_scratch || (which != 0 && which != 1) || spin_limit < 1 || spin_limit > kSpinLimit) return GS_ERR_ARG;
+    if (!d_scratch || which < 0 || which > 2 || spin_limit < 1 || spin_limit > kSpinLimit) return GS_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // d_scratch: [0] error word, [64, 64 + 512) look-back flags of partitions 0 and 1
     if (cudaMemsetAsync(d_scratch, 0, GS_SELFTEST_SCRATCH_BYTES, s) != cudaSuccess) return GS_ERR_CUDA;
+    if (which == 2) {
+        // the tcgen05 blend's mbarrier wait (render_tc5.cu)
+        if (launch_tc5_wait_selftest(s, d_scratch, spin_limit) != cudaSuccess) {
+            cudaGetLastError();
+            return GS_ERR_CUDA;
+        }
+        count_launch();
+        return GS_OK;
+    }
     lookback_selftest_kernel<<<1, which == 0 ? 32 : 256, 0, s>>>(which, d_scratch + 64, d_scratch, spin_limit);
     count_launch();
     if (cudaPeekAtLastError() != cudaSuccess) {

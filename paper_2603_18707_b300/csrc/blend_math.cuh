@@ -17,6 +17,25 @@
 
 namespace gs {
 
+// Arguments of the forward blend kernels (render.cu, render_tc5.cu).
+struct RenderArgs {
+    const float4 *rec;
+    const uint32_t *vals;
+    const uint2 *ranges;
+    uint32_t n_records;
+    float bg0, bg1, bg2;
+    float *out;
+    float *final_T;
+    uint32_t *last;
+    uint32_t *n_eval;
+};
+
+// The tensor-core quadric on tcgen05 (render_tc5.cu): one CTA per 16x16 tile.
+cudaError_t launch_render_tc5(int kind, cudaStream_t s, const CamTable &t, const CfgDev &c, const RenderArgs &g);
+// Self-test of its bounded mbarrier wait: a wait that no arrival completes
+// gives up after `limit` polls and ORs GS_ERR_TIMEOUT into *err.
+cudaError_t launch_tc5_wait_selftest(cudaStream_t s, uint32_t *err, int limit);
+
 struct BlendCoef {
     float4 a; // ux, uy, u0, vy
     float4 b; // v0, p0, p1, p2 (f1, exp: x_cut)

@@ -58,18 +58,6 @@ constexpr bool blend_branchless()
     return GS_BLEND_BRANCHLESS == 1 || (GS_BLEND_BRANCHLESS == 2 && KIND == GS_K_EXP);
 }
 
-struct RenderArgs {
-    const float4 *rec;
-    const uint32_t *vals;
-    const uint2 *ranges;
-    uint32_t n_records;
-    float bg0, bg1, bg2;
-    float *out;
-    float *final_T;
-    uint32_t *last;
-    uint32_t *n_eval;
-};
-
 // FP16x2 alpha of a pixel pair (u_a, u_b computed in FP32, sharing v^2):
 // Q = u^2 + v^2 and the opacity-folded kernel in packed half2 FMAs, before
 // the alpha_max clamp (which the caller applies in FP32: 0.99 is not a half).
@@ -574,7 +562,7 @@ extern "C" gs_status gs_render(void *stream, const gs_camera *cams, int32_t ncam
     const int ppt = cfg->px_per_thread;
     if (ppt != 1 && ppt != 2 && ppt != 4) return GS_ERR_ARG;
     if (cfg->batch < 1 || cfg->batch > kMaxBatch) return GS_ERR_ARG;
-    if (cfg->tensor_alpha != 0 && cfg->tensor_alpha != 1) return GS_ERR_ARG;
+    if (cfg->tensor_alpha < 0 || cfg->tensor_alpha > 2) return GS_ERR_ARG;
     if (cfg->tensor_alpha && (cfg->tile_w != 16 || cfg->tile_h != 16 || cfg->fp16x2 || d_work))
         return GS_ERR_UNSUPPORTED; // tensor-core variant: 16x16 tiles, FP32, one CTA per tile
     const bool half = cfg->fp16x2 != 0;
@@ -596,7 +584,9 @@ extern "C" gs_status gs_render(void *stream, const gs_camera *cams, int32_t ncam
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     uint32_t *work = static_cast<uint32_t *>(d_work);
     cudaError_t e;
-    if (cfg->tensor_alpha) {
+    if (cfg->tensor_alpha == 2) {
+        e = launch_render_tc5(cfg->kind, s, t, c, g);
+    } else if (cfg->tensor_alpha) {
         switch (cfg->kind) {
         case GS_K_EXP: render_tc_kernel<GS_K_EXP><<<t.total_tiles, 256, 0, s>>>(t, c, g); break;
         case GS_K_POLY1: render_tc_kernel<GS_K_POLY1><<<t.total_tiles, 256, 0, s>>>(t, c, g); break;

