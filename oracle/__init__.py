@@ -260,7 +260,9 @@ def render_tiled(sc: dict, cam: Camera, cfg: Config, bg=(0.0, 0.0, 0.0), tiles=N
     """Tile-binned render; ``tiles``: iterable of tile ids (default all).
     Returns image, final T, last contributor, evaluations per pixel, list
     length per tile (and, with ``with_margin``, the per-pixel decision
-    margin: relative distance of the closest skip / stop decision)."""
+    margin: distance of the closest skip / stop decision from its threshold,
+    relative to the threshold plus the change a 0.3 px shift of the splats
+    causes; diagnostic, see gs_oracle.c)."""
     if s2d is None:
         s2d = project(sc, cam, cfg)
     P = np.asarray(sc["means"]).size // 3

@@ -495,6 +495,12 @@ static double quadric(const orc_splat2d *s, double px, double py)
  * Returns the number of entries evaluated; *last = position + 1 of the last
  * contributing entry (0 if none).
  */
+/* Diagnostic scale of the decision margin (pixels): an FP32 renderer holds
+ * pixel coordinates up to 4096 to within 2.4e-4 px, so its alphas move as if
+ * each splat were shifted by up to that much; 0.3 px times the margin's 1e-3
+ * flip band is 3e-4 px. */
+#define ORC_MARGIN_PX 0.3
+
 static long long composite_pixel(const orc_splat2d *s, const int *order, long long n,
                                  const orc_config *cfg, double x0, double px, double py,
                                  const double bg[3], double out[3], double *Tout, long long *last,
@@ -503,24 +509,38 @@ static long long composite_pixel(const orc_splat2d *s, const int *order, long lo
     double T = 1.0, C[3] = {0.0, 0.0, 0.0};
     long long evaluated = n;
     double m = INFINITY;
+    double tsens = 0.0; /* diagnostic: sum of |grad alpha| / (1 - alpha) over blended entries */
     *last = 0;
     for (long long j = 0; j < n; ++j) {
         const orc_splat2d *g = &s[order[j]];
         double Q = quadric(g, px, py);
         double alpha = g->opacity * orc_kernel(cfg, x0, Q);
-        /* diagnostic only: relative distance of this entry's skip decision */
-        double me = fabs(alpha - cfg->eps) / cfg->eps;
-        if (me < m) m = me;
+        /* diagnostic only: distance of this entry's skip decision from its
+         * threshold, relative to eps plus the change of alpha over
+         * ORC_MARGIN_PX (|grad alpha| = o' |k'(Q)| |grad Q|) */
+        double ga = 0.0;
+        if (margin) {
+            double dx = px - g->mean2d[0], dy = py - g->mean2d[1];
+            double hx = g->conic[0] * dx + g->conic[1] * dy, hy = g->conic[1] * dx + g->conic[2] * dy;
+            ga = g->opacity * fabs(orc_kernel_deriv(cfg, x0, Q)) * 2.0 * sqrt(hx * hx + hy * hy);
+            double me = fabs(alpha - cfg->eps) / (cfg->eps + ORC_MARGIN_PX * ga);
+            if (me < m) m = me;
+        }
         if (alpha > cfg->alpha_max) alpha = cfg->alpha_max;
         if (alpha < cfg->eps) continue;
         double Tn = T * (1.0 - alpha);
-        double ms = fabs(Tn - cfg->t_min) / cfg->t_min;
-        if (ms < m) m = ms;
+        if (margin) {
+            /* the stop decision: against t_min plus the change of T (1 - alpha)
+             * over the same shift of this and every earlier blended entry */
+            double ms = fabs(Tn - cfg->t_min) / (cfg->t_min + ORC_MARGIN_PX * (T * ga + Tn * tsens));
+            if (ms < m) m = ms;
+        }
         if (Tn < cfg->t_min) {
             evaluated = j + 1;
             break;
         }
         for (int ch = 0; ch < 3; ++ch) C[ch] += g->color[ch] * alpha * T;
+        if (margin) tsens += ga / (1.0 - alpha);
         T = Tn;
         *last = j + 1;
     }
@@ -557,9 +577,12 @@ void orc_render_untiled(int P, const orc_splat2d *s, const orc_camera *cam,
  * the untiled render exactly. tiles_sel lists the tile ids to render
  * (n_tiles_sel < 0: all tiles); pixels of other tiles are left untouched.
  * n_eval: entries evaluated per pixel; list_len: list length per tile;
- * margin (optional, diagnostic): per pixel, the smallest relative distance of
- * any skip (alpha vs eps) or stop (T (1 - alpha) vs t_min) decision from its
- * threshold — pixels where a lower-precision renderer may decide otherwise.
+ * margin (optional, diagnostic): per pixel, the smallest distance of any skip
+ * (alpha vs eps) or stop (T (1 - alpha) vs t_min) decision from its
+ * threshold, relative to the threshold plus the change the decided quantity
+ * undergoes when the splats move by ORC_MARGIN_PX — pixels where a
+ * lower-precision renderer may decide otherwise (below 1e-3: within 0.1 % of
+ * the threshold, or within 3e-4 px of the boundary).
  */
 void orc_render_tiled(int P, const orc_splat2d *s, const orc_camera *cam,
                       const orc_config *cfg, const double bg[3],

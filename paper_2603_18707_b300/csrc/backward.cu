@@ -103,6 +103,9 @@ blend_backward_kernel(const __grid_constant__ CamTable cams, const __grid_consta
                       float bg2, const float *__restrict__ final_T, const uint32_t *__restrict__ last,
                       const float *__restrict__ grad_out, float *__restrict__ grad2d)
 {
+    // the forward's FP32 alpha arithmetic (render.cu): f1 and exp fold their
+    // Q coefficient into the affine forms
+    constexpr bool FOLD = folds_p1<KIND>();
     extern __shared__ float4 s_dyn[];
     const int B = blockDim.x;
     float4 *s_g = s_dyn; // mu'x, mu'y, o', 1 / o'
@@ -172,7 +175,7 @@ blend_backward_kernel(const __grid_constant__ CamTable cams, const __grid_consta
             if (v >= n_records) v = 0;
             s_id[threadIdx.x] = v;
             const float4 r0 = rec[3 * (size_t)v + 0], r1 = rec[3 * (size_t)v + 1];
-            const BlendCoef kc = make_coef<KIND>(cfg, r0, r1, rec[3 * (size_t)v + 2], ox, oy);
+            const BlendCoef kc = make_coef<KIND, FOLD>(cfg, r0, r1, rec[3 * (size_t)v + 2], ox, oy);
             s_g[threadIdx.x] = make_float4(r0.x, r0.y, r0.z, 1.f / r0.z);
             s_q[threadIdx.x] = r1;
             s_ka[threadIdx.x] = kc.a;
@@ -187,14 +190,19 @@ blend_backward_kernel(const __grid_constant__ CamTable cams, const __grid_consta
             const float p3 = (KIND == GS_K_POLY3) ? s_kc[jj].w : 0.f;
             const float ub = fmaf(ka.y, yl, ka.z);
             const float vv = fmaf(ka.w, yl, kb.x);
-            const float v2 = vv * vv;
+            const float v2 = FOLD ? fmaf(-vv, vv, kb.y) : vv * vv; // FOLD: beta
             float Q[PPT], a0[PPT];
             bool con[PPT], anyc = false;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 const float u = fmaf(ka.x, xl[k], ub);
-                Q[k] = fmaf(u, u, v2);
-                a0[k] = alpha_of_q<KIND>(cfg, kb, p3, Q[k]);
+                if constexpr (FOLD) {
+                    Q[k] = 0.f; // f1 and exp need no Q for their slope
+                    a0[k] = alpha_folded<KIND>(v2, u);
+                } else {
+                    Q[k] = fmaf(u, u, v2);
+                    a0[k] = alpha_of_q<KIND>(cfg, kb, p3, Q[k]);
+                }
                 con[k] = (uint32_t)j < L[k] && fminf(amax, a0[k]) >= eps;
                 anyc |= con[k];
             }

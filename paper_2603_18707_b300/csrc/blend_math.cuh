@@ -36,15 +36,33 @@ cudaError_t launch_render_tc5(int kind, cudaStream_t s, const CamTable &t, const
 // gives up after `limit` polls and ORs GS_ERR_TIMEOUT into *err.
 cudaError_t launch_tc5_wait_selftest(cudaStream_t s, uint32_t *err, int limit);
 
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 struct BlendCoef {
     float4 a; // ux, uy, u0, vy
     float4 b; // v0, p0, p1, p2 (f1, exp: x_cut)
     float4 c; // red, green, blue, p3
 };
 
-// rec0 = (mu'x, mu'y, o', depth), rec1 = (A, B, C, x_cut), rec2 = (r, g, b, rho);
-// (ox, oy): pixel coordinates of the tile's corner.
+// f1 and exp in the FP32 blend: their Q coefficient p1 is negative, and
+// sigma = sqrt(-p1) is folded into the two affine forms (s = sigma u,
+// t = sigma v), so that p0 + p1 Q = beta - s^2 with beta = p0 - t^2 per row:
+// two FMAs per pixel for the exponent / the alpha (FOLD below).
 template <int KIND>
+constexpr bool folds_p1()
+{
+    return KIND == GS_K_POLY1 || KIND == GS_K_EXP;
+}
+
+// rec0 = (mu'x, mu'y, o', depth), rec1 = (A, B, C, x_cut), rec2 = (r, g, b, rho);
+// (ox, oy): pixel coordinates of the tile's corner. FOLD: a and b.x carry
+// sigma (f1, exp only).
+template <int KIND, bool FOLD = false>
 __device__ __forceinline__ BlendCoef make_coef(const CfgDev &cfg, float4 r0, float4 r1, float4 r2,
                                                float ox, float oy)
 {
@@ -73,15 +91,25 @@ __device__ __forceinline__ BlendCoef make_coef(const CfgDev &cfg, float4 r0, flo
     if (KIND == GS_K_POLY1 || KIND == GS_K_EXP) p2 = (cfg.cull == GS_CULL_LEGACY3) ? INFINITY : r1.w;
     k.b = make_float4(-vy * my, p0, p1, p2);
     k.c = make_float4(r2.x, r2.y, r2.z, p3);
+    if constexpr (FOLD) {
+        static_assert(folds_p1<KIND>(), "only f1 and exp fold their Q coefficient");
+        // sqrt(log2(e) / 2) for exp; f1's c1 < 0 (its root is finite and positive)
+        const float sg = (KIND == GS_K_EXP) ? 0.84932180028801904f : sqrtf(-p1);
+        k.a = make_float4(sg * k.a.x, sg * k.a.y, sg * k.a.z, sg * k.a.w);
+        k.b.x *= sg;
+    }
     return k;
 }
 
-__device__ __forceinline__ float ex2_approx(float x)
+// FOLD form: o' k(Q) before the alpha_max clamp, from beta = p0 - t^2 and s.
+template <int KIND>
+__device__ __forceinline__ float alpha_folded(float beta, float s)
 {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
+    const float e = fmaf(-s, s, beta);
+    if (KIND == GS_K_EXP) return ex2_approx(e);
+    return e;
 }
+
 
 // o' k(Q) before the alpha_max clamp.
 template <int KIND>

@@ -133,6 +133,13 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
     const __half2 x0h = __float2half2_rn(fminf(cfg.x0, 60000.f));
     const __half2 f3bh = __float2half2_rn(cfg.f3b), f3gh = __float2half2_rn(cfg.f3g);
     const bool factored = KIND == GS_K_POLY3 && cfg.f3_factored;
+    // FP32 f1 / exp: sigma folded into the affine forms (blend_math.cuh), so
+    // the row term v2 below is beta = p0 - t^2 and the pixel's exponent /
+    // alpha is beta - s^2
+    constexpr bool FOLD = !HALF && folds_p1<KIND>();
+    // skip threshold of the folded per-run test: 2^-8 below eps (exp: its
+    // exponent), far more than the rounding of the run's bound on |s|
+    const float fold_skip = KIND == GS_K_EXP ? log2f(eps * (1.f - 1.f / 256.f)) : eps * (1.f - 1.f / 256.f);
     // skip threshold of the per-run test: just below eps, so that rounding
     // never skips an entry a pixel takes (the FP16x2 path takes the FP32
     // path's decisions, so the same test serves both)
@@ -143,8 +150,8 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
             if (base + i < n) {
                 uint32_t v = g.vals[rg.x + base + i];
                 if (v >= g.n_records) v = 0; // only after a timed-out sort wait
-                const BlendCoef k = make_coef<KIND>(cfg, g.rec[3 * (size_t)v + 0], g.rec[3 * (size_t)v + 1],
-                                                    g.rec[3 * (size_t)v + 2], ox, oy);
+                const BlendCoef k = make_coef<KIND, FOLD>(cfg, g.rec[3 * (size_t)v + 0],
+                                                          g.rec[3 * (size_t)v + 1], g.rec[3 * (size_t)v + 2], ox, oy);
                 s_a[i] = k.a;
                 s_b[i] = k.b;
                 s_c[i] = k.c;
@@ -167,7 +174,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
             const float4 b = s_b[j];
             const float ub = fmaf(a.y, y, a.z);
             const float vv = fmaf(a.w, y, b.x);
-            const float v2 = vv * vv;
+            const float v2 = FOLD ? fmaf(-vv, vv, b.y) : vv * vv; // FOLD: beta
             const float p3 = (KIND == GS_K_POLY3) ? s_c[j].w : 0.f; // the cubic's top coefficient
             if (PPT > 1 && cfg.monotone) {
                 // smallest Q over this thread's run of pixels: u is affine
@@ -184,9 +191,12 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                 const float ua = fmaf(a.x, lx + 0.5f, ub), uz = fmaf(a.x, lx + PPT - 0.5f, ub);
                 const float um = ((ua > 0.f) != (uz > 0.f)) ? 0.f : fminf(fabsf(ua), fabsf(uz));
 #endif
-                if constexpr (KIND == GS_K_POLY1 || KIND == GS_K_EXP) {
+                if constexpr (FOLD) {
+                    // the run's largest exponent / alpha is beta - sm^2
+                    if (fmaf(-um, um, v2) < fold_skip) continue;
+                } else if constexpr (KIND == GS_K_POLY1 || KIND == GS_K_EXP) {
                     // beyond the record's cut x_cut: no pixel's exact alpha
-                    // reaches eps (FP16x2 too: it then skips what FP32 skips)
+                    // reaches eps (FP16x2: it then skips what FP32 skips)
                     if (fmaf(um, um, v2) > b.w) continue;
                 } else {
                     if (alpha_of_q<KIND>(cfg, b, p3, fmaf(um, um, v2)) < eps_skip) continue;
@@ -195,11 +205,11 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
             const float4 col = s_c[j];
             const uint32_t pos = base + j + 1;
             if constexpr (HALF) {
-                // alphas in packed half, decisions as the FP32 path takes them:
-                // d bounds |alpha(half) - alpha(FP32)| for this entry, so an
-                // alpha further than d from eps is on the FP32 alpha's side of
-                // it; within d (rare) the pixel's alpha is recomputed with the
-                // FP32 path's arithmetic, and so is it where T (1 - alpha) lies
+                // alphas in packed half, decisions in FP32: d bounds
+                // |alpha(half) - alpha(FP32)| for this entry, so an alpha
+                // further than d from eps is on the FP32 alpha's side of it;
+                // within d (rare) the pixel's alpha is recomputed in FP32
+                // (Q form, alpha_of_q), and so is it where T (1 - alpha) lies
                 // within T d of t_min (the stop decision)
                 const uint4 hp = s_h[j];
                 const __half2 v2h = __float2half2_rn(v2);
@@ -250,8 +260,10 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                 // min(alpha_max, x) < eps exactly when x < eps: the clamp
                 // is applied only to entries that are blended
                 const float u = fmaf(a.x, xs[k], ub);
-                const float Q = fmaf(u, u, v2);
-                al[k] = alpha_of_q<KIND>(cfg, b, p3, Q);
+                if constexpr (FOLD)
+                    al[k] = alpha_folded<KIND>(v2, u);
+                else
+                    al[k] = alpha_of_q<KIND>(cfg, b, p3, fmaf(u, u, v2));
             }
             if constexpr (blend_branchless<KIND>()) {
 #pragma unroll
