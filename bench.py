@@ -170,6 +170,9 @@ def parse():
     p.add_argument("--tile", type=str, default=None, help="tile shape WxH, e.g. 16x16")
     p.add_argument("--rect", choices=["aabb", "circle", "ellipse"], default=None,
                    help="tile binning around the support ellipse")
+    p.add_argument("--tensor-alpha", type=int, choices=[0, 1, 2], default=0,
+                   help="blend variant for --profile: 1 mma.sync, 2 tcgen05 tensor-core quadric")
+    p.add_argument("--fp16x2", action="store_true", help="FP16x2 blend for --profile")
     p.add_argument("--leg", choices=list(LEGS), default=None,
                    help="run only this extra leg and print its result (profiling; no headline line)")
     p.add_argument("--profile", choices=["poly1", "exp", "poly2", "poly3"], default=None,
@@ -377,6 +380,10 @@ def run_ours(a, world, rank, local):
         over["tile"] = tuple(int(v) for v in a.tile.split("x"))
     if a.rect:
         over["rect"] = a.rect
+    if a.profile and a.tensor_alpha:
+        over["tensor_alpha"] = a.tensor_alpha
+    if a.profile and a.fp16x2:
+        over["fp16x2"] = 1
     if a.profile:
         # profiling mode: one arm, buffers sized, then exactly `steps` passes
         r = render.Rasterizer(cams, api.make_config(a.profile, "opacity", **over), P)

@@ -322,7 +322,7 @@ def test_persistent_graph_mixed_batch_matches_oracle(gs, orc):
     shapes = [autotune.config_overrides(tuned), {"tile": (32, 16), "batch": 256, "px_per_thread": 4}]
     osc = orc.activate(raw)
     rng = np.random.default_rng(3)
-    checked = 0
+    checked = n_near = n_px = 0
     for over in shapes:
         cfg = api.make_config("poly1", "opacity", **over)
         R = render.Rasterizer(cams, cfg, P, persistent=True)
@@ -356,7 +356,8 @@ def test_persistent_graph_mixed_batch_matches_oracle(gs, orc):
                 far = margin[ys, xs] >= NEAR_MARGIN
                 err = np.abs(img[ys, xs].astype(np.float64) - ref[ys, xs]).max(-1)
                 assert err[far].max(initial=0.0) < TOL_FP32, (c, t, over)
-                assert (~far).sum() <= 0.05 * far.size + 2
+                n_near += int((~far).sum())
+                n_px += far.size
                 G = vals[rg[base + t, 0]:rg[base + t, 1]] - c * P
                 O = oracle_tile_list(o, t, tx)
                 assert set(O.tolist()) <= set(G.tolist())
@@ -365,3 +366,4 @@ def test_persistent_graph_mixed_batch_matches_oracle(gs, orc):
             base += tx * ty
         del graph, R
     assert checked >= 2 * 10 * 2
+    assert n_near < 0.03 * n_px  # threshold flips are a small minority of the checked pixels
