@@ -61,7 +61,10 @@ def blend_source_hash() -> str:
 #       python bench.py --profile poly1 --steps 2 --warmup 1
 # and pipe utilisation from a --set full capture of the same kernel (1M
 # splats x 4 cameras; the kernel's code, not the scene, sets these).
-BLEND_CAPTURE = {"src_hash": None, "traffic": None, "ncu": None}
+BLEND_CAPTURE = {"src_hash": "39dd05ea9ae3c9ce", "traffic": 731217152 + 625938176,
+                 "ncu": {"issue_active": 0.791, "fma_pipe": 0.323, "alu_pipe": 0.505, "lanes_active_of_32": 16.41,
+                         "warps_active": 0.444,
+                         "source": "ncu --set full, render_kernel<POLY1, 4, FP32>, 1M splats x 4 cameras"}}
 
 
 def hbm_peak_gbs() -> tuple[float, str]:
