@@ -62,14 +62,31 @@ def _masked_weights(orc, sc, oc, kind, shape, seed=9):
     return w
 
 
-def _check(gpu, ref, rel=1e-3, floor=2e-4):
+def _check(gpu, ref, rel=1e-3, floor=1e-5, name=None):
+    """Every gradient entry within 1e-3 of the oracle's, relative; entries
+    near zero within 1e-5 of the tensor's largest (FP32 accumulation over
+    many pixels leaves an absolute error of ~1e-7 of the largest, measured on
+    the finite-difference sub-case, so 1e-5 is no relative bound for them but
+    a tight absolute one). The worst relative error of the entries above the
+    floor and the worst floor-relative error are reported."""
+    import json
+    import os
+    stats = {}
     for k in ("means", "scales", "quats", "opacities", "sh"):
         a, b = gpu[k].reshape(-1), ref[k].reshape(-1)
         scale = np.abs(b).max()
         assert scale > 0, k
         err = np.abs(a - b)
-        assert np.all(err <= rel * np.abs(b) + floor * scale), (k, float((err / scale).max()))
+        big = np.abs(b) > floor * scale / rel
+        stats[k] = {"max_rel_above_floor": float((err[big] / np.abs(b[big])).max(initial=0.0)),
+                    "max_abs_over_largest": float((err / scale).max())}
+        assert np.all(err <= rel * np.abs(b) + floor * scale), (k, stats[k])
         assert np.linalg.norm(a - b) <= rel * np.linalg.norm(b), k
+    rep = os.environ.get("GS_REPORT_DIR")
+    if rep and name:
+        os.makedirs(rep, exist_ok=True)
+        with open(os.path.join(rep, "backward_vs_oracle.jsonl"), "a") as f:
+            f.write(json.dumps({"case": name, **stats}) + "\n")
 
 
 @pytest.mark.parametrize("kind,cull", [("poly1", "opacity"), ("exp", "universal"),
@@ -85,7 +102,7 @@ def test_backward_matches_oracle_reverse_pass(gs, orc, kind, cull):
     w = _masked_weights(orc, sc, oc, kind, (48, 56, 3))
     gpu, _ = _gpu_grads(api, render, raw, [cam], kind, cull, w, bg)
     ref = orc.render_backward(sc, oc, orc.make_config(kind, KIND_COEFFS[kind], cull), w, bg)
-    _check(gpu, ref)
+    _check(gpu, ref, name=f"{kind}-{cull}")
 
 
 @pytest.mark.parametrize("tile", [(8, 8), (32, 8), (32, 16)])
@@ -102,7 +119,7 @@ def test_backward_tile_shapes(gs, orc, tile):
     w = _masked_weights(orc, sc, oc, "poly1", (48, 56, 3))
     gpu, _ = _gpu_grads(api, render, raw, [cam], "poly1", "opacity", w, bg, tile=tile)
     ref = orc.render_backward(sc, oc, orc.make_config("poly1", KIND_COEFFS["poly1"], "opacity"), w, bg)
-    _check(gpu, ref)
+    _check(gpu, ref, name=f"tile{tile[0]}x{tile[1]}")
 
 
 def test_backward_matches_finite_differences(gs, orc):
@@ -137,7 +154,7 @@ def test_backward_matches_finite_differences(gs, orc):
             if len(vals) < 2:
                 continue
             fd = (vals[0] - vals[1]) / (2 * h)
-            assert abs(gpu[name][idx] - fd) <= 1e-3 * abs(fd) + 2e-4 * scale, (name, idx, gpu[name][idx], fd)
+            assert abs(gpu[name][idx] - fd) <= 1e-3 * abs(fd) + 1e-5 * scale, (name, idx, gpu[name][idx], fd)
             checked += 1
     assert checked >= 80
 
@@ -277,7 +294,7 @@ def test_differentiable_1M_scene_sampled_tiles(gs, orc):
     w[margin < NEAR_MARGIN] = 0.0
     gpu, _ = _gpu_grads(api, render, raw, [cam], "poly1", "opacity", w, (0.0, 0.0, 0.0))
     ref = orc.render_backward(sc, oc, cfg, w, (0.0, 0.0, 0.0))
-    _check(gpu, ref)
+    _check(gpu, ref, name="1M-1024-sampled-tiles")
 
 
 def test_backward_finite_differences_256_splats_64x64(gs, orc):
