@@ -18,9 +18,13 @@
 // tcgen05.mma.kind::tf32 (M = 128 pixels, N = kT5B splats, K = 8: two pixel
 // halves x {lo, hi}) into a TMEM accumulator of 2 kT5B columns and commits
 // them to an mbarrier. Every thread waits on it (bounded), reads its pixel's
-// row of Q with tcgen05.ld (warp w reaches TMEM lanes 32 (w mod 4) ..; half
-// w / 4 is the column block), and composites in FP32 with the kernel,
-// thresholds and order of the FP32 path (alpha_of_q). Forward only.
+// row with tcgen05.ld (warp w reaches TMEM lanes 32 (w mod 4) ..; half w / 4
+// is the column block), and composites in FP32 with the thresholds and order
+// of the FP32 path. f1 and exp are affine in Q, so their opacity-folded
+// coefficients go into the weights (W' = p1 W, plus p0 on the constant
+// monomial): the accumulator holds f1's alpha, or exp's exponent, directly,
+// and a pixel-entry below eps costs one compare. f'2 and f3 read Q and
+// evaluate their polynomial (alpha_of_q). Forward only.
 #include <algorithm>
 
 #include "blend_math.cuh"
@@ -122,6 +126,8 @@ __global__ void __launch_bounds__(256, 1)
 render_tc5_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
                   const __grid_constant__ RenderArgs g)
 {
+    // f1 and exp: the MMA yields alpha / the exponent (see the file header)
+    constexpr bool AFFINE = KIND == GS_K_POLY1 || KIND == GS_K_EXP;
     extern __shared__ __align__(1024) unsigned char t5_smem[];
     T5Smem &S = *reinterpret_cast<T5Smem *>(t5_smem);
     const int gtile = blockIdx.x;
@@ -172,6 +178,11 @@ render_tc5_kernel(const __grid_constant__ CamTable cams, const __grid_constant__
     bool active = px < cm.W && py < cm.H;
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
     uint32_t lastc = 0, ne = n, parity = 0;
+    // affine kernels: the accumulator's value that can reach eps (exp: its
+    // exponent, 2^-8 below log2 eps so that ex2's rounding decides), +inf once
+    // the pixel has stopped or lies off the frame
+    const float thr_on = KIND == GS_K_EXP ? log2f(eps) - 1.f / 256.f : eps;
+    float thr = active ? thr_on : INFINITY;
     bool failed = false;
     for (uint32_t base = 0; base < n; base += kT5B) {
         if (__syncthreads_count(active) == 0) break;
@@ -196,6 +207,13 @@ render_tc5_kernel(const __grid_constant__ CamTable cams, const __grid_constant__
                 w[3] = -2.f * gx;
                 w[4] = -2.f * gy;
                 w[5] = fmaf(dx0, gx, dy0 * gy);
+                if (AFFINE) { // alpha (f1) or exponent (exp) = p0 + p1 Q
+#pragma unroll
+                    for (int kk = 0; kk < 6; ++kk) w[kk] *= k.b.z;
+                    w[5] += k.b.y;
+                }
+            } else if (AFFINE) {
+                w[5] = -1e30f; // padding: below any threshold
             }
             uint32_t hi[8], lo[8];
 #pragma unroll
@@ -234,26 +252,52 @@ render_tc5_kernel(const __grid_constant__ CamTable cams, const __grid_constant__
             if (!__any_sync(0xffffffffu, active)) break; // warp-uniform: tcgen05.ld is warp-wide
             uint32_t q[16];
             tmem_ld16(taddr + (uint32_t)c0, q);
+            if constexpr (AFFINE) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                if (!active || c0 + j >= cnt) continue;
-                const float4 cj = S.coef_c[c0 + j];
-                const float al0 = alpha_of_q<KIND>(cfg, S.coef_b[c0 + j], cj.w, __uint_as_float(q[j]));
-                if (!(al0 >= eps)) continue;
-                const float al = fminf(amax, al0);
-                const float Tn = fmaf(-al, T, T);
-                const uint32_t pos = base + c0 + j + 1;
-                if (Tn < tmin) {
-                    active = false;
-                    ne = pos;
-                    continue;
+                for (int j = 0; j < 16; ++j) {
+                    const float x = __uint_as_float(q[j]);
+                    if (!(x >= thr)) continue; // padding entries lie far below
+                    const float al0 = KIND == GS_K_EXP ? ex2_approx(x) : x;
+                    if (!(al0 >= eps)) continue;
+                    const float4 cj = S.coef_c[c0 + j];
+                    const float al = fminf(amax, al0);
+                    const float Tn = fmaf(-al, T, T);
+                    const uint32_t pos = base + c0 + j + 1;
+                    if (Tn < tmin) {
+                        active = false;
+                        thr = INFINITY;
+                        ne = pos;
+                        continue;
+                    }
+                    const float wgt = al * T;
+                    C0 = fmaf(cj.x, wgt, C0);
+                    C1 = fmaf(cj.y, wgt, C1);
+                    C2 = fmaf(cj.z, wgt, C2);
+                    T = Tn;
+                    lastc = pos;
                 }
-                const float wgt = al * T;
-                C0 = fmaf(cj.x, wgt, C0);
-                C1 = fmaf(cj.y, wgt, C1);
-                C2 = fmaf(cj.z, wgt, C2);
-                T = Tn;
-                lastc = pos;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    if (!active || c0 + j >= cnt) continue;
+                    const float4 cj = S.coef_c[c0 + j];
+                    const float al0 = alpha_of_q<KIND>(cfg, S.coef_b[c0 + j], cj.w, __uint_as_float(q[j]));
+                    if (!(al0 >= eps)) continue;
+                    const float al = fminf(amax, al0);
+                    const float Tn = fmaf(-al, T, T);
+                    const uint32_t pos = base + c0 + j + 1;
+                    if (Tn < tmin) {
+                        active = false;
+                        ne = pos;
+                        continue;
+                    }
+                    const float wgt = al * T;
+                    C0 = fmaf(cj.x, wgt, C0);
+                    C1 = fmaf(cj.y, wgt, C1);
+                    C2 = fmaf(cj.z, wgt, C2);
+                    T = Tn;
+                    lastc = pos;
+                }
             }
         }
     }
