@@ -122,7 +122,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&q)[16])
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(256, 4) // four CTAs per SM: the TMEM and shared-memory plan
 render_tc5_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
                   const __grid_constant__ RenderArgs g)
 {
@@ -184,6 +184,20 @@ render_tc5_kernel(const __grid_constant__ CamTable cams, const __grid_constant__
     const float thr_on = KIND == GS_K_EXP ? log2f(eps) - 1.f / 256.f : eps;
     float thr = active ? thr_on : INFINITY;
     bool failed = false;
+    // the records of a batch are gathered one batch ahead (by the threads
+    // that stage them), so that the loads overlap the previous batch's MMA
+    // and compositing
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
+    const auto gather = [&](uint32_t b) {
+        if (tid < kT5B && b + tid < n) {
+            uint32_t v = g.vals[rg.x + b + tid];
+            if (v >= g.n_records) v = 0; // only after a timed-out sort wait
+            r0 = g.rec[3 * (size_t)v + 0];
+            r1 = g.rec[3 * (size_t)v + 1];
+            r2 = g.rec[3 * (size_t)v + 2];
+        }
+    };
+    gather(0);
     for (uint32_t base = 0; base < n; base += kT5B) {
         if (__syncthreads_count(active) == 0) break;
         const int cnt = (int)min((uint32_t)kT5B, n - base);
@@ -191,10 +205,6 @@ render_tc5_kernel(const __grid_constant__ CamTable cams, const __grid_constant__
             float w[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             float4 bb = make_float4(0.f, 0.f, 0.f, 0.f), cc = bb;
             if (tid < cnt) {
-                uint32_t v = g.vals[rg.x + base + tid];
-                if (v >= g.n_records) v = 0; // only after a timed-out sort wait
-                const float4 r0 = g.rec[3 * (size_t)v + 0], r1 = g.rec[3 * (size_t)v + 1];
-                const float4 r2 = g.rec[3 * (size_t)v + 2];
                 const BlendCoef k = make_coef<KIND>(cfg, r0, r1, r2, ox, oy);
                 bb = k.b;
                 cc = k.c;
@@ -241,6 +251,7 @@ render_tc5_kernel(const __grid_constant__ CamTable cams, const __grid_constant__
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
                          : "memory");
         }
+        gather(base + kT5B); // the next batch's records, while the MMAs run
         const bool ok = mbar_wait(mbar, parity, kT5Spin);
         parity ^= 1u;
         if (__syncthreads_or(!ok)) {
