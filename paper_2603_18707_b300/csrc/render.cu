@@ -47,10 +47,12 @@ constexpr int blend_unroll()
 #define GS_RENDER_MIN_BLOCKS 4 // 256-thread CTAs per SM the register budget must allow (64 registers: measured fastest)
 #endif
 // Per-pixel update: predicated (no branch per pixel) or branching. 0: branch
-// for every kernel, 1: predicate for every kernel, 2: predicate for exp only
-// (measured: exp, which blends more entries per pixel, gains ~8%; f1 loses ~7%).
+// for every kernel, 1: predicate for every kernel, 2: predicate for exp only.
+// Measured with the folded alpha (one-stream 16-camera pass): branching for
+// every kernel, f1 8.07 ms / exp 10.95 ms; predicated exp 11.24 ms;
+// predicated f1 8.34 ms.
 #ifndef GS_BLEND_BRANCHLESS
-#define GS_BLEND_BRANCHLESS 2
+#define GS_BLEND_BRANCHLESS 0
 #endif
 template <int KIND>
 constexpr bool blend_branchless()
