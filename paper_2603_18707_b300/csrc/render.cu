@@ -43,6 +43,9 @@ constexpr int blend_unroll()
 #ifndef GS_SKIP_MID
 #define GS_SKIP_MID 1 // per-thread skip bound from the run's centre (1) or its two ends (0)
 #endif
+#ifndef GS_PERSIST_CAP
+#define GS_PERSIST_CAP 0 // persistent blend: CTAs per SM at most (0: as many as fit)
+#endif
 #ifndef GS_RENDER_MIN_BLOCKS
 #define GS_RENDER_MIN_BLOCKS 4 // 256-thread CTAs per SM the register budget must allow (64 registers: measured fastest)
 #endif
@@ -534,6 +537,7 @@ cudaError_t launch2(int threads, cudaStream_t s, const CamTable &t, const CfgDev
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_persistent_kernel<KIND, PPT, HALF>,
                                                       threads, 0) != cudaSuccess)
         return cudaGetLastError();
+    if (GS_PERSIST_CAP > 0) per_sm = std::min(per_sm, GS_PERSIST_CAP);
     const int grid = std::max(1, std::min(t.total_tiles, sms * std::max(per_sm, 1)));
     cudaError_t e = cudaMemsetAsync(work, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
