@@ -53,18 +53,18 @@ def blend_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-# ncu figures of the f1 blend (render_kernel<POLY1, 4, FP32>): DRAM bytes (read
-# + write) of one launch on the default workload (3M splats, 16 cameras at
-# 1920x1080, scene in Z-order), from
+# ncu figures of the f1 blend (render_persistent_kernel<POLY1, 4, FP32>): DRAM
+# bytes (read + write) of one launch on the default workload (3M splats, 16
+# cameras at 1920x1080, scene in Z-order), from
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
-#       --clock-control none -k regex:render_kernel -c 2
+#       --clock-control none -k regex:render_persistent -c 2
 #       python bench.py --profile poly1 --steps 2 --warmup 1
 # and pipe utilisation from a --set full capture of the same kernel (1M
 # splats x 4 cameras; the kernel's code, not the scene, sets these).
-BLEND_CAPTURE = {"src_hash": "39dd05ea9ae3c9ce", "traffic": 731217152 + 625938176,
-                 "ncu": {"issue_active": 0.791, "fma_pipe": 0.323, "alu_pipe": 0.505, "lanes_active_of_32": 16.41,
-                         "warps_active": 0.444,
-                         "source": "ncu --set full, render_kernel<POLY1, 4, FP32>, 1M splats x 4 cameras"}}
+BLEND_CAPTURE = {"src_hash": "8bb353a4474f0d49", "traffic": 731547136 + 628287488,
+                 "ncu": {"issue_active": 0.815, "fma_pipe": 0.330, "alu_pipe": 0.520, "lanes_active_of_32": 16.39,
+                         "warps_active": 0.479,
+                         "source": "ncu --set full, render_persistent_kernel<POLY1, 4, FP32>, 1M splats x 4 cameras"}}
 
 
 def hbm_peak_gbs() -> tuple[float, str]:
