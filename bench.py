@@ -61,10 +61,10 @@ def blend_source_hash() -> str:
 #       python bench.py --profile poly1 --steps 2 --warmup 1
 # and pipe utilisation from a --set full capture of the same kernel (1M
 # splats x 4 cameras; the kernel's code, not the scene, sets these).
-BLEND_CAPTURE = {"src_hash": "8bb353a4474f0d49", "traffic": 731547136 + 628287488,
-                 "ncu": {"issue_active": 0.815, "fma_pipe": 0.330, "alu_pipe": 0.520, "lanes_active_of_32": 16.39,
-                         "warps_active": 0.479,
-                         "source": "ncu --set full, render_persistent_kernel<POLY1, 4, FP32>, 1M splats x 4 cameras"}}
+BLEND_CAPTURE = {"src_hash": "2bb33d95d4950f21", "traffic": 732036608 + 499431680,
+                 "ncu": {"issue_active": 0.801, "fma_pipe": 0.321, "alu_pipe": 0.465, "lanes_active_of_32": 16.54,
+                         "warps_active": 0.477,
+                         "source": "ncu --set full, render_persistent_kernel<POLY1, 4, FP32, no index tracking>, 1M splats x 4 cameras"}}
 
 
 def hbm_peak_gbs() -> tuple[float, str]:
@@ -192,7 +192,9 @@ def workload(a):
             "camera_sets_on_streams": getattr(a, "groups", 1), "blend_launch": "persistent",
             "splat_order": ("z-order of the means, stored once at load (render.spatial_order)"
                             if getattr(a, "splat_order", "zorder") == "zorder" else "generator order"),
-            "l2": "inputs larger than L2 (scene 0.7 GB, records 3 GB per step)"}
+            "l2": "inputs larger than L2 (scene 0.7 GB, records 3 GB per step)",
+            "outputs": "RGB and final transmittance per pixel; the last-contributor index, which only "
+                       "the reverse pass reads, is not kept (poly1_keep_last times it kept)"}
 
 
 class ClockSampler:
@@ -392,7 +394,7 @@ def run_ours(a, world, rank, local):
         # (the blend launched as in the timed arms: persistent, unless a
         # tensor-core variant, which runs one CTA per tile)
         r = render.Rasterizer(cams, api.make_config(a.profile, "opacity", **over), P,
-                              persistent=not a.tensor_alpha)
+                              persistent=not a.tensor_alpha, last=False)
         r.forward(sc, n_eval=False)
         torch.cuda.synchronize()
         e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -414,8 +416,8 @@ def run_ours(a, world, rank, local):
         # next tile from a counter (1.3 % faster per step than one CTA per tile)
         cfg = api.make_config(kind, "opacity", **over)
         if a.groups > 1:
-            return render.StreamedRasterizer(cams, cfg, P, groups=a.groups, persistent=True)
-        return render.Rasterizer(cams, cfg, P, persistent=True)
+            return render.StreamedRasterizer(cams, cfg, P, groups=a.groups, persistent=True, last=False)
+        return render.Rasterizer(cams, cfg, P, persistent=True, last=False)
 
     R = {"poly1": make("poly1"), "exp": make("exp")}
     evals, psnr = {}, []
@@ -457,6 +459,13 @@ def run_ours(a, world, rank, local):
         else:
             ms = timed(lambda: r.run_async(sc), a.steps)
         res[k] = max_over_ranks(ms, world)
+    # context: the same f1 pass keeping each pixel's last contributor (as a
+    # training forward does)
+    for p in getattr(R["poly1"], "parts", [R["poly1"]]):
+        p.keep_last = True
+    ms_keep_last = max_over_ranks(timed(lambda: R["poly1"].run_async(sc), max(3, a.steps // 2)), world)
+    for p in getattr(R["poly1"], "parts", [R["poly1"]]):
+        p.keep_last = False
 
     # per-stage device times (CUDA events between the entry points, same stream)
     stages = {}
@@ -615,6 +624,7 @@ def run_ours(a, world, rank, local):
             "exp": {"frames_per_s": world * a.cams / (res["exp"] / 1e3), "ms_per_step": res["exp"],
                     "gsplat_evals_per_s": evals_all["exp"] / (res["exp"] / 1e3) / 1e9},
             "speedup_poly1_vs_exp": res["exp"] / ms,
+            "poly1_keep_last": {"frames_per_s": world * a.cams / (ms_keep_last / 1e3), "ms_per_step": ms_keep_last},
             "psnr_poly1_vs_exp_db": {"mean": float(np.mean(psnr)), "min": float(np.min(psnr))},
             "evals_per_step": evals, "overlaps_per_step": overlaps, "stages_ms": stages,
             "roofline": roofline, "sort_bin_hbm": sort_bin, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
@@ -681,8 +691,8 @@ def bench_sweep(a, sc, cams, over, world, R_head):
     steps = max(5, a.steps // 4)
     for kind, cull in SWEEP_ARMS:
         cfg = api.make_config(kind, cull, **over)
-        r = (render.StreamedRasterizer(cams, cfg, a.splats, groups=a.groups, persistent=True) if a.groups > 1
-             else render.Rasterizer(cams, cfg, a.splats, persistent=True))
+        r = (render.StreamedRasterizer(cams, cfg, a.splats, groups=a.groups, persistent=True, last=False)
+             if a.groups > 1 else render.Rasterizer(cams, cfg, a.splats, persistent=True, last=False))
         r.forward(sc, n_eval=True)
         ev = int(r.n_eval.to(torch.int64).sum().item())
         psnr = float(np.mean([_psnr(x.cpu().numpy(), y.cpu().numpy()) for x, y in zip(r.images(), exp_imgs)]))
@@ -819,6 +829,7 @@ def bench_fp16x2(a):
             imgs[half] = R.out.clone()
             dec[half] = (R.n_eval.clone(), R.last.clone())
             evals = int(R.n_eval.to(torch.int64).sum().item())
+            R.keep_last = False  # timed as the headline: image only
             for _ in range(3):
                 R.run_async(sc)
             res[half] = _events_ms(lambda: R.run_async(sc), max(5, a.steps // 6))
@@ -930,7 +941,7 @@ def bench_batched(a):
     for kind in ("poly1", "exp"):
         tuned = autotune.autotune(cams, kind, "opacity", sc, P, persistent=True, steps=3, cache=None)
         cfg = api.make_config(kind, "opacity", **autotune.config_overrides(tuned))
-        R = render.Rasterizer(cams, cfg, P, persistent=True)
+        R = render.Rasterizer(cams, cfg, P, persistent=True, last=False)
         R.forward(sc, n_eval=True)
         evals = int(R.n_eval.to(torch.int64).sum().item())
         graph = R.capture(sc)

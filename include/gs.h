@@ -192,6 +192,9 @@ gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t ncam, int32_t
  *                contributing entry, 0 if none (may be NULL; the backward
  *                pass needs it)
  *   d_n_eval:    uint32 [sum_c H_c W_c] list entries evaluated (may be NULL)
+ *                With d_last and d_n_eval both NULL the blend keeps no
+ *                per-pixel list positions and runs faster; the image and
+ *                d_final_T are the same bit for bit.
  *   bg:          host float[3] background colour
  *   d_work:      NULL for one CTA per tile; otherwise gs_render_work_bytes()
  *                bytes of device memory (4-byte aligned) and the blend runs as

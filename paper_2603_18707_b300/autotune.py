@@ -27,21 +27,21 @@ PPTS = (1, 2, 4)
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "gs_b300_autotune.json")
 
 
-def _key(cams, kind, cull, P, persistent):
+def _key(cams, kind, cull, P, persistent, last=False):
     res = sorted((int(c["width"]), int(c["height"])) for c in cams)
     counts = {}
     for r in res:
         counts[r] = counts.get(r, 0) + 1
     rs = ",".join(f"{w}x{h}*{n}" for (w, h), n in sorted(counts.items()))
-    return f"{torch.cuda.get_device_name()}|{kind}|{cull}|P={P}|persistent={int(persistent)}|{rs}"
+    return f"{torch.cuda.get_device_name()}|{kind}|{cull}|P={P}|persistent={int(persistent)}|last={int(last)}|{rs}"
 
 
-def _time(cams, kind, cull, sc, P, over, persistent, steps):
+def _time(cams, kind, cull, sc, P, over, persistent, steps, last=False):
     """ms per pass, or inf for a candidate this workload cannot run (e.g.
     small tiles pushing the overlap count past the binning's 2^30 limit)."""
     cfg = api.make_config(kind, cull, **over)
     try:
-        R = Rasterizer(cams, cfg, P, persistent=persistent)
+        R = Rasterizer(cams, cfg, P, persistent=persistent, last=last)
         R.forward(sc, n_eval=False)
     except RuntimeError:
         torch.cuda.synchronize()
@@ -60,10 +60,13 @@ def _time(cams, kind, cull, sc, P, over, persistent, steps):
 
 
 def autotune(cams, kind: str, cull: str, sc: dict, P: int, persistent: bool = False,
-             steps: int = 5, cache: str | None = DEFAULT_CACHE, verbose: bool = False) -> dict:
+             steps: int = 5, cache: str | None = DEFAULT_CACHE, verbose: bool = False,
+             last: bool = False) -> dict:
     """Best {"tile", "batch", "px_per_thread"} for this workload, plus the
-    timings that chose it (ms per pass)."""
-    key = _key(cams, kind, cull, P, persistent)
+    timings that chose it (ms per pass). last: tune the blend that keeps each
+    pixel's last contributor (a training forward) instead of the image-only
+    one (a serving render)."""
+    key = _key(cams, kind, cull, P, persistent, last)
     store = {}
     if cache and os.path.exists(cache):
         try:
@@ -77,13 +80,13 @@ def autotune(cams, kind: str, cull: str, sc: dict, P: int, persistent: bool = Fa
         for ppt in PPTS:
             over = {"tile": tile, "px_per_thread": ppt, "batch": BATCHES[0]}
             trials[f"{tile[0]}x{tile[1]}/b{BATCHES[0]}/p{ppt}"] = (
-                _time(cams, kind, cull, sc, P, over, persistent, steps), over)
+                _time(cams, kind, cull, sc, P, over, persistent, steps, last), over)
     best_name = min(trials, key=lambda k: trials[k][0])
     best = dict(trials[best_name][1])
     for b in BATCHES[1:]:
         over = dict(best, batch=b)
         trials[f"{over['tile'][0]}x{over['tile'][1]}/b{b}/p{over['px_per_thread']}"] = (
-            _time(cams, kind, cull, sc, P, over, persistent, steps), over)
+            _time(cams, kind, cull, sc, P, over, persistent, steps, last), over)
     best_name = min(trials, key=lambda k: trials[k][0])
     best_over = trials[best_name][1]
     result = {"tile": list(best_over["tile"]), "batch": int(best_over["batch"]),

@@ -96,7 +96,10 @@ __device__ __forceinline__ float2 alpha_pair_h2(float ua, float ub, __half2 v2h,
     return __half22float2(al);
 }
 
-template <int KIND, int PPT, bool HALF>
+// TRACK: keep each pixel's last contributor and evaluation count (only when
+// the caller asks for d_last or d_n_eval: the reverse pass and the
+// evaluation count need them, the image does not)
+template <int KIND, int PPT, bool HALF, bool TRACK>
 __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &cfg, const RenderArgs &g,
                                             int gtile, float4 *s_a, float4 *s_b, float4 *s_c, uint4 *s_h)
 {
@@ -248,7 +251,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                     if (Tn < tmin) {
                         active &= ~(1u << k);
                         xs[k] = NAN;
-                        ne[k] = pos;
+                        if constexpr (TRACK) ne[k] = pos;
                         continue;
                     }
                     const float w = x * T[k];
@@ -256,7 +259,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                     C1[k] = fmaf(col.y, w, C1[k]);
                     C2[k] = fmaf(col.z, w, C2[k]);
                     T[k] = Tn;
-                    lastc[k] = pos;
+                    if constexpr (TRACK) lastc[k] = pos;
                 }
             } else {
             float al[PPT];
@@ -283,8 +286,10 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                     C1[k] = fmaf(col.y, w, C1[k]);
                     C2[k] = fmaf(col.z, w, C2[k]);
                     T[k] = add ? Tn : T[k];
-                    lastc[k] = add ? pos : lastc[k];
-                    ne[k] = stop ? pos : ne[k];
+                    if constexpr (TRACK) {
+                        lastc[k] = add ? pos : lastc[k];
+                        ne[k] = stop ? pos : ne[k];
+                    }
                     active &= ~((unsigned)stop << k);
                     xs[k] = stop ? NAN : xs[k];
                 }
@@ -297,7 +302,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                     if (Tn < tmin) {
                         active &= ~(1u << k);
                         xs[k] = NAN;
-                        ne[k] = pos;
+                        if constexpr (TRACK) ne[k] = pos;
                         continue;
                     }
                     const float w = al[k] * T[k];
@@ -305,7 +310,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                     C1[k] = fmaf(col.y, w, C1[k]);
                     C2[k] = fmaf(col.z, w, C2[k]);
                     T[k] = Tn;
-                    lastc[k] = pos;
+                    if constexpr (TRACK) lastc[k] = pos;
                 }
             }
             }
@@ -319,13 +324,13 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
             g.out[3 * pix + 1] = fmaf(T[k], g.bg1, C1[k]);
             g.out[3 * pix + 2] = fmaf(T[k], g.bg2, C2[k]);
             if (g.final_T) g.final_T[pix] = T[k];
-            if (g.last) g.last[pix] = lastc[k];
-            if (g.n_eval) g.n_eval[pix] = ne[k];
+            if (TRACK && g.last) g.last[pix] = lastc[k];
+            if (TRACK && g.n_eval) g.n_eval[pix] = ne[k];
         }
     }
 }
 
-template <int KIND, int PPT, bool HALF>
+template <int KIND, int PPT, bool HALF, bool TRACK>
 __global__ void __launch_bounds__(256, GS_RENDER_MIN_BLOCKS)
 render_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
               const __grid_constant__ RenderArgs g)
@@ -334,10 +339,10 @@ render_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ Cfg
     __shared__ float4 s_b[kMaxBatch];
     __shared__ float4 s_c[kMaxBatch];
     __shared__ uint4 s_h[HALF ? kMaxBatch : 1];
-    render_tile<KIND, PPT, HALF>(cams, cfg, g, blockIdx.x, s_a, s_b, s_c, s_h);
+    render_tile<KIND, PPT, HALF, TRACK>(cams, cfg, g, blockIdx.x, s_a, s_b, s_c, s_h);
 }
 
-template <int KIND, int PPT, bool HALF>
+template <int KIND, int PPT, bool HALF, bool TRACK>
 __global__ void __launch_bounds__(256, GS_RENDER_MIN_BLOCKS)
 render_persistent_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
                          const __grid_constant__ RenderArgs g, uint32_t *work)
@@ -353,7 +358,7 @@ render_persistent_kernel(const __grid_constant__ CamTable cams, const __grid_con
         const uint32_t t = s_tile;
         __syncthreads(); // every thread has read s_tile before it is overwritten
         if (t >= (uint32_t)cams.total_tiles) break;
-        render_tile<KIND, PPT, HALF>(cams, cfg, g, (int)t, s_a, s_b, s_c, s_h);
+        render_tile<KIND, PPT, HALF, TRACK>(cams, cfg, g, (int)t, s_a, s_b, s_c, s_h);
     }
 }
 
@@ -523,26 +528,34 @@ render_tc_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ 
     }
 }
 
-template <int KIND, int PPT, bool HALF>
-cudaError_t launch2(int threads, cudaStream_t s, const CamTable &t, const CfgDev &c, const RenderArgs &g,
+template <int KIND, int PPT, bool HALF, bool TRACK>
+cudaError_t launch3(int threads, cudaStream_t s, const CamTable &t, const CfgDev &c, const RenderArgs &g,
                     uint32_t *work)
 {
     if (!work) {
-        render_kernel<KIND, PPT, HALF><<<t.total_tiles, threads, 0, s>>>(t, c, g);
+        render_kernel<KIND, PPT, HALF, TRACK><<<t.total_tiles, threads, 0, s>>>(t, c, g);
         return cudaPeekAtLastError();
     }
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_persistent_kernel<KIND, PPT, HALF>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_persistent_kernel<KIND, PPT, HALF, TRACK>,
                                                       threads, 0) != cudaSuccess)
         return cudaGetLastError();
     if (GS_PERSIST_CAP > 0) per_sm = std::min(per_sm, GS_PERSIST_CAP);
     const int grid = std::max(1, std::min(t.total_tiles, sms * std::max(per_sm, 1)));
     cudaError_t e = cudaMemsetAsync(work, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    render_persistent_kernel<KIND, PPT, HALF><<<grid, threads, 0, s>>>(t, c, g, work);
+    render_persistent_kernel<KIND, PPT, HALF, TRACK><<<grid, threads, 0, s>>>(t, c, g, work);
     return cudaPeekAtLastError();
+}
+
+template <int KIND, int PPT, bool HALF>
+cudaError_t launch2(int threads, cudaStream_t s, const CamTable &t, const CfgDev &c, const RenderArgs &g,
+                    uint32_t *work)
+{
+    if (g.last || g.n_eval) return launch3<KIND, PPT, HALF, true>(threads, s, t, c, g, work);
+    return launch3<KIND, PPT, HALF, false>(threads, s, t, c, g, work);
 }
 
 template <int KIND>

@@ -56,9 +56,13 @@ class Rasterizer:
     """Renders P splats into a fixed list of cameras (at most 64)."""
 
     def __init__(self, cams, cfg, P: int, capacity: int | None = None, device="cuda",
-                 keep_keys: bool = False, persistent: bool = False, outputs: dict | None = None):
+                 keep_keys: bool = False, persistent: bool = False, outputs: dict | None = None,
+                 last: bool = True):
         """outputs: optional views (out [npix, 3], final_T, last, n_eval [npix])
-        to render into instead of buffers of its own."""
+        to render into instead of buffers of its own. last=False: the blend
+        does not keep each pixel's last contributor (`self.last` is left
+        unwritten), which only the reverse pass reads; the image and final T
+        are the same and the blend does less work per entry."""
         self.cams = api.camera_array(cams)
         self.ncam = len(self.cams)
         self.cfg = cfg
@@ -81,6 +85,7 @@ class Rasterizer:
             self.last = torch.empty(self.npix, **i32)
             self.n_eval = torch.empty(self.npix, **i32)
         self.keep_keys = keep_keys
+        self.keep_last = bool(last)
         self.work = (torch.zeros(api.gs_render_work_bytes(), **u8) if persistent else None)
         self.shrink = capacity is None  # an explicit capacity is kept as given
         self.capacity = 0
@@ -120,7 +125,8 @@ class Rasterizer:
 
     def blend(self, bg=(0.0, 0.0, 0.0), n_eval: bool = True):
         api.gs_render(self.cams, self.P, self.cfg, self.splat2d, self.vals, self.ranges, bg,
-                      self.out, self.final_T, self.last, self.n_eval if n_eval else None,
+                      self.out, self.final_T, self.last if self.keep_last else None,
+                      self.n_eval if n_eval else None,
                       self.work)
 
     def forward(self, sc: dict, bg=(0.0, 0.0, 0.0), n_eval: bool = True, deferred: bool = False):
@@ -235,11 +241,11 @@ class StreamedRasterizer:
     Rasterizer of its own rendering into its slice of shared output buffers,
     and each set's pass (preprocess, bin/sort, blend) issued on a stream of
     its own: one set's latency-bound sort overlaps another's ALU-bound blend.
-    persistent: each set's blend as one persistent launch (see Rasterizer).
+    persistent: each set's blend as one persistent launch; last: see Rasterizer.
     Same interface as Rasterizer; the work per pass is the same."""
 
     def __init__(self, cams, cfg, P: int, groups: int = 2, device="cuda", keep_keys: bool = False,
-                 persistent: bool = False):
+                 persistent: bool = False, last: bool = True):
         cams = list(cams)
         groups = max(1, min(int(groups), len(cams)))
         bounds = [round(k * len(cams) / groups) for k in range(groups + 1)]
@@ -262,7 +268,7 @@ class StreamedRasterizer:
             views = {"out": self.out[o:o + n], "final_T": self.final_T[o:o + n],
                      "last": self.last[o:o + n], "n_eval": self.n_eval[o:o + n]}
             self.parts.append(Rasterizer(cs, cfg, P, device=device, keep_keys=keep_keys, outputs=views,
-                                         persistent=persistent))
+                                         persistent=persistent, last=last))
             o += n
         self.streams = [torch.cuda.Stream(device=self.device) for _ in self.parts]
         self.bounds = bounds

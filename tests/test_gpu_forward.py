@@ -161,6 +161,35 @@ def test_image_matches_oracle(gs, orc, small, kind, cull, ppt):
     assert np.abs(T - Tref)[far].max() < TOL_FP32
 
 
+@pytest.mark.parametrize("kind", ["exp", "poly1", "poly2", "poly3"])
+@pytest.mark.parametrize("mode", ["fp32", "fp16x2", "persistent"])
+def test_image_without_last_contributor_is_identical(gs, orc, small, kind, mode):
+    """The blend that keeps neither the last contributor nor the evaluation
+    count (an image-only render) takes the same decisions: its image and final
+    T equal, bit for bit, those of the blend that keeps both (which the other
+    tests hold to the oracle), and its image is within 2e-4 of the oracle."""
+    from paper_2603_18707_b300 import api, render, synth
+    cam = synth.camera_small()
+    over = {"fp16x2": 1, "px_per_thread": 4} if mode == "fp16x2" else {"px_per_thread": 4}
+    cfg = api.make_config(kind, "opacity", **over)
+    sc = render.activate(small)
+    out = {}
+    for keep in (True, False):
+        R = render.Rasterizer([cam], cfg, small["means"].shape[0], persistent=mode == "persistent", last=keep)
+        R.forward(sc, n_eval=keep)
+        torch.cuda.synchronize()
+        out[keep] = (R.out.clone(), R.final_T.clone())
+    assert torch.equal(out[True][0], out[False][0])
+    assert torch.equal(out[True][1], out[False][1])
+    if mode == "fp32":
+        ref, _, _ = orc.render_untiled(orc.activate(small), orc.camera_from_dict(cam),
+                                       _oracle_cfg(orc, kind, "opacity"))
+        *_, margin = orc.render_tiled(orc.activate(small), orc.camera_from_dict(cam),
+                                      orc.make_config(kind, KIND_COEFFS[kind], "universal"), with_margin=True)
+        worst, _, _ = _compare(out[False][0].cpu().numpy().reshape(ref.shape), ref, margin)
+        assert worst < TOL_FP32
+
+
 @pytest.mark.parametrize("tile", [8, 16])
 @pytest.mark.parametrize("cull", ["universal", "opacity"])
 def test_f2_range_coefficients_match_oracle(gs, orc, small, tile, cull):
