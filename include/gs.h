@@ -157,25 +157,31 @@ gs_status gs_preprocess(void *stream, const gs_camera *cams, int32_t ncam, int32
  * (tx, ty) is base_c + ty * ceil(W_c / tile_w) + tx, cameras in order. */
 int64_t gs_total_tiles(const gs_camera *cams, int32_t ncam, const gs_config *cfg);
 
-/* Workspace bytes for gs_bin_sort with N = ncam * P records, room for
- * `capacity` splat-tile overlaps and `total_tiles` tiles. */
-size_t gs_bin_sort_workspace_bytes(int64_t n_records, int64_t capacity, int64_t total_tiles);
+/* Workspace bytes for gs_bin_sort with these cameras and tile shape, P
+ * splats and room for `capacity` splat-tile overlaps; 0 for invalid
+ * arguments (the checks of gs_bin_sort). */
+size_t gs_bin_sort_workspace_bytes(const gs_camera *cams, int32_t ncam, int32_t P,
+                                   const gs_config *cfg, int64_t capacity);
 
 /* Depth-ordered tile binning of the records written by gs_preprocess.
  * Result: for global tile t, d_vals[d_ranges[2t] .. d_ranges[2t+1]) are the
  * record indices (c * P + i) of the splats whose rectangle contains t, in
  * increasing (depth, i) order — a stable sort of the 64-bit keys
  * (tile << 32 | depth bits) 3DGS uses. Implemented as a stable LSD radix sort
- * of the drawn records by depth followed by a stable LSD radix sort of the
- * emitted overlaps by tile id, both Onesweep (one pass per 8-bit digit,
- * decoupled look-back with a bounded wait).
+ * of each camera's drawn records by depth (Onesweep: one pass per 8-bit
+ * digit, decoupled look-back with a bounded wait), then two stable splits of
+ * the depth-sorted records: by tile row (one span per covered row) and by
+ * tile column, the latter writing every record index to its final place.
+ * Tiles of a camera: at most 2048 per row and per column.
  *   d_vals:      uint32 [capacity]
- *   d_ranges:    uint32 [2 * total_tiles] (start, end) per tile
+ *   d_ranges:    uint32 [2 * total_tiles] (start, end) per tile; (0, 0)
+ *                for a tile that no record covers
  *   d_keys64:    optional uint64 [capacity] (may be NULL): the sorted keys
  *   d_count:     optional uint32 [3] (may be NULL): drawn records, overlaps
  *                stored, overlaps counted (the capacity needed)
  * Overlaps beyond `capacity` are dropped and GS_ERR_CAPACITY is raised in the
- * workspace error word. At most 2^30 - 1 records and overlaps per call. */
+ * workspace error word (the ranges then stay inside [0, capacity)). At most
+ * 2^30 - 1 records and overlaps per call. */
 gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t ncam, int32_t P,
                       const gs_config *cfg, const void *d_splat2d, int64_t capacity,
                       void *d_workspace, size_t workspace_bytes, uint32_t *d_vals,
@@ -248,8 +254,8 @@ gs_status gs_render_backward(void *stream, const gs_camera *cams, int32_t ncam, 
  * Same arguments, results and errors as gs_bin_sort, minus the workspace: the
  * scratch is one fixed array of GS_NOALLOC_WORKSPACE_BYTES in static device
  * memory, held until the process exits. Sizes whose workspace
- * (gs_bin_sort_workspace_bytes(ncam * P, capacity, tiles): about 17 bytes
- * per record plus 13 bytes per overlap of capacity) would not fit are
+ * (gs_bin_sort_workspace_bytes(cams, ncam, P, cfg, capacity): about 18 bytes
+ * per record plus 8 bytes per overlap of capacity) would not fit are
  * rejected with GS_ERR_ARG before anything is launched.
  *  - Set-up happens in the first call on each device: with that device
  *    current it looks up the array's device address and caches it. Under

@@ -53,7 +53,7 @@ _SIGS = {
     "gs_preprocess": (_i32, [_vp, C.POINTER(GsCamera), _i32, _i32, _vp, _vp, _vp, _vp, _vp, _i32,
                              C.POINTER(GsConfig), _vp]),
     "gs_total_tiles": (_i64, [C.POINTER(GsCamera), _i32, C.POINTER(GsConfig)]),
-    "gs_bin_sort_workspace_bytes": (_sz, [_i64, _i64, _i64]),
+    "gs_bin_sort_workspace_bytes": (_sz, [C.POINTER(GsCamera), _i32, _i32, C.POINTER(GsConfig), _i64]),
     "gs_bin_sort": (_i32, [_vp, C.POINTER(GsCamera), _i32, _i32, C.POINTER(GsConfig), _vp, _i64,
                            _vp, _sz, _vp, _vp, _vp, _vp]),
     "gs_bin_sort_noalloc": (_i32, [_vp, C.POINTER(GsCamera), _i32, _i32, C.POINTER(GsConfig), _vp,

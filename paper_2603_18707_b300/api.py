@@ -102,8 +102,9 @@ def gs_total_tiles(cams, cfg: GsConfig) -> int:
     return int(lib().gs_total_tiles(arr, len(arr), C.byref(cfg)))
 
 
-def gs_bin_sort_workspace_bytes(n_records: int, capacity: int, total_tiles: int) -> int:
-    return int(lib().gs_bin_sort_workspace_bytes(n_records, capacity, total_tiles))
+def gs_bin_sort_workspace_bytes(cams, P: int, cfg: GsConfig, capacity: int) -> int:
+    arr = camera_array(cams)
+    return int(lib().gs_bin_sort_workspace_bytes(arr, len(arr), int(P), C.byref(cfg), int(capacity)))
 
 
 def gs_grad2d_bytes(ncam: int, P: int) -> int:

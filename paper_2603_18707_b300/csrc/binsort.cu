@@ -3,30 +3,38 @@
 // Result: per global tile, the records whose support rectangle covers it,
 // in increasing (depth, record index) order. That is the order a stable sort
 // of 3DGS's 64-bit keys (tile << 32 | depth bits) over records emitted in
-// index order gives. It is produced here without ever materialising 64-bit
-// keys:
+// index order gives. It is produced here without materialising keys per
+// overlap and without sorting overlaps at all:
 //   1. compact   drawn records (tiles > 0) -> (depth bits, record index),
-//                in index order (single-pass scan with decoupled look-back);
-//                also histograms the four depth digits
-//   2. sort      stable LSD radix sort of those by depth: 4 Onesweep passes
-//   3. emit      walk the depth-sorted records, scan their tile counts and
-//                write one (tile id, record index) pair per covered tile;
-//                warp-cooperative so that every store is coalesced; also
-//                histograms the tile-id digits
-//   4. sort      stable LSD radix sort of the pairs by tile id: 1 pass of 8
-//                bits, 2 of 8, 2 of 9 or 3 of 8-9 bits, whatever covers the
-//                tile ids
-//   5. ranges    first / one-past-last position of every tile id
-// The depth digits are sorted once per record instead of once per overlap,
-// which moves far fewer bytes than sorting the 64-bit keys directly.
+//                in index order, i.e. grouped by camera (single-pass scan
+//                with decoupled look-back); also the per-camera histograms
+//                of the four depth digits, the per-camera start offsets, and
+//                per camera a difference array of the tile rows the records
+//                cover
+//   2. plan      one CTA: partition tables of the record and row segments,
+//                span count and first span of every tile row
+//   3. sort      stable LSD radix sort by depth within each camera: 4
+//                Onesweep passes of 8 bits over camera segments
+//   4. rows      split the depth-sorted records of each camera by tile row:
+//                one span (record, first and last tile column) per covered
+//                row, stored grouped by (camera, row) in depth order
+//   5. count     tile counts from the spans (per-row difference arrays)
+//   6. scan      exclusive scan of the tile counts: the per-tile ranges
+//   7. columns   split the spans of each row by tile column, writing every
+//                record index straight to its final place in its tile's list
+// Steps 4 and 7 are one "stable split" each: items (records, then spans)
+// that cover a contiguous range of digits (rows, then columns) are expanded
+// in item order and ranked per digit, Onesweep style: each CTA takes the
+// next partition of a segment (camera, then tile row) from a counter,
+// publishes its per-digit counts and resolves its offsets by decoupled
+// look-back over the segment's earlier partitions. The depth digits are
+// sorted once per record instead of once per overlap, and each overlap is
+// written once, as its final 4-byte record index.
 //
-// Onesweep (one kernel per digit): each CTA claims the next partition of 5120
-// keys from an atomic counter, ranks its keys per digit with warp
-// match/ballot, publishes per-digit counts and resolves its global offsets by
-// decoupled look-back over earlier partitions (kLookWindow predecessors per
-// load round), then scatters through shared memory so that global stores are
-// contiguous per digit. Every spin-wait is bounded: on expiry it raises
-// GS_ERR_TIMEOUT in the workspace error word and carries on with what it has.
+// Every spin-wait is bounded: on expiry it raises GS_ERR_TIMEOUT in the
+// workspace error word and carries on with what it has; stores are checked
+// against the buffers' capacities, so the results are then wrong but every
+// access stays in bounds.
 #include <algorithm>
 #include <utility>
 
@@ -50,22 +58,8 @@ constexpr int kSpinLimit = 1 << 20;
 #ifndef GS_LOOK_WINDOW
 #define GS_LOOK_WINDOW 1
 #endif
-#ifndef GS_EMIT_MIN_BLOCKS
-// 0: no register cap from the occupancy target. 8 (32 registers, some
-// spills to L1) measured fastest: the emission waits on memory, and 8 CTAs
-// per SM hide more of it than 4 (64 registers, no spills) or 6.
-#define GS_EMIT_MIN_BLOCKS 8
-#endif
-#if GS_EMIT_MIN_BLOCKS
-#define GS_EMIT_BOUNDS __launch_bounds__(256, GS_EMIT_MIN_BLOCKS)
-#else
-#define GS_EMIT_BOUNDS __launch_bounds__(256)
-#endif
-#ifndef GS_EMIT_RUNS
-#define GS_EMIT_RUNS 1 // tile-digit histogram adds of the higher digits per run of equal digits
-#endif
-#ifndef GS_EMIT_ITEMS
-#define GS_EMIT_ITEMS 8
+#ifndef GS_SPLIT_BLOCKS
+#define GS_SPLIT_BLOCKS 4 // resident CTAs per SM of the persistent split kernels
 #endif
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = GS_SORT_ITEMS;
@@ -75,29 +69,41 @@ constexpr int kSortTile = kSortThreads * kSortItems; // keys per partition
 #endif
 constexpr int kCompactVec = GS_COMPACT_VEC;          // uint4 loads per lane
 constexpr int kCompactTile = 256 * 4 * kCompactVec;  // records per partition
-constexpr int kEmitItems = GS_EMIT_ITEMS;
-constexpr int kEmitTile = 256 * kEmitItems;          // records per partition
-constexpr int kHistSlot = 512;                       // histogram entries per pass
+constexpr int kRowItems = kSortItems;                // records per thread of the row split
+constexpr int kRowTile = 256 * kRowItems;            // records per row-split partition
+static_assert(kRowTile == kSortTile, "the row split reuses the depth sort's partition table");
+constexpr int kColItems = 20;                        // spans per thread of the column split
+constexpr int kColTile = 256 * kColItems;            // spans per column-split partition
+constexpr int kScanItems = 16;
+constexpr int kScanTile = 256 * kScanItems;          // tiles per scan partition
+constexpr int kMaxDigits = 2048;                     // tile rows / columns per camera (16384 px / 8)
 constexpr int kLookWindow = GS_LOOK_WINDOW;
 
 enum Counter {
     CTR_COMPACT = 0,
     CTR_DEPTH = 1, // 4 passes
-    CTR_EMIT = 5,
-    CTR_TILE = 6,  // up to 3 passes
-    CTR_COUNT = 10
+    CTR_ROWS = 5,
+    CTR_COUNT_COLS = 6,
+    CTR_SCAN = 7,
+    CTR_COLS = 8,
+    CTR_N = 10
 };
 
 struct WsHeader {
     uint32_t err;
-    uint32_t n_vis;      // drawn records
-    uint32_t n_over;     // overlaps stored (<= capacity)
-    uint32_t n_over_raw; // overlaps counted
-    uint32_t ctr[CTR_COUNT];
-    uint32_t pad[64 - 4 - CTR_COUNT];
+    uint32_t n_vis;       // drawn records
+    uint32_t n_over;      // overlaps stored (<= capacity)
+    uint32_t n_over_raw;  // overlaps counted (the capacity needed)
+    uint32_t n_span;      // row spans
+    uint32_t n_rec_parts; // partitions of the record segments
+    uint32_t n_span_parts;
+    uint32_t pad0;
+    unsigned long long k_total; // sum of the drawn records' tile counts
+    uint32_t ctr[CTR_N];
+    uint32_t pad[64 - 10 - CTR_N];
 };
+static_assert(sizeof(WsHeader) == 256, "header size");
 
-// Digit plan of the tile-id sort.
 // Division of n < 2^31 by a fixed d >= 1 as a multiply-high and a shift:
 // with s = ceil(log2 d) and m = ceil(2^(31+s) / d) < 2^32, floor(n m / 2^(31+s))
 // = floor(n / d), since the error n (m - 2^(31+s)/d) / 2^(31+s) < n / 2^(31+s)
@@ -122,31 +128,25 @@ struct FastDiv {
     __device__ __forceinline__ uint32_t div(uint32_t n) const { return sh < 0 ? n : __umulhi(n, m) >> sh; }
 };
 
-struct TilePlan {
-    int passes;
-    int bits[3];
-    int shift[3];
+// Per-call geometry of the binning, a kernel parameter. Tile rows of all
+// cameras are numbered back to back with one padding row after each camera
+// ("padded rows"): camera c's row y is padded row gpad + y, and its padding
+// row gpad + tiles_y closes its difference array.
+struct BinCam {
+    int tiles_x, tiles_y;
+    int tile_base; // first global tile id
+    int gpad;      // first padded row
+    int W, H;
 };
-
-TilePlan tile_plan(int64_t total_tiles)
-{
-    // as few passes as 9-bit digits allow, and within them as many 8-bit
-    // digits as possible (an 8-bit pass is ~25% cheaper per key); the widest
-    // digit first (the look-back state is sized by it). Up to 27 bits
-    // (< 2^30 tiles is checked by the caller).
-    int b = 1;
-    while (((int64_t)1 << b) < total_tiles) ++b;
-    TilePlan p{};
-    p.passes = std::max(1, (b + 8) / 9);
-    const int nine = std::max(0, b - 8 * p.passes);
-    int s = 0;
-    for (int i = 0; i < p.passes; ++i) {
-        p.bits[i] = i < nine ? 9 : 8;
-        p.shift[i] = s;
-        s += p.bits[i];
-    }
-    return p;
-}
+struct BinPlan {
+    int ncam;
+    int G; // padded rows: sum of (tiles_y + 1)
+    int max_tx, max_ty;
+    int tile_w, tile_h;
+    uint32_t P;
+    FastDiv pdiv;
+    BinCam cam[kMaxCams];
+};
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p)
 {
@@ -183,6 +183,19 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x)
         if (lane >= o) x += y;
     }
     return x;
+}
+
+// Lane that owns sub-item q of a warp's expansion: the number of lanes whose
+// inclusive prefix of sub-item counts is <= q (binary search over the lanes).
+__device__ __forceinline__ int owner_lane(uint32_t incl, uint32_t q)
+{
+    int e = 0;
+#pragma unroll
+    for (int sft = 16; sft > 0; sft >>= 1) {
+        const uint32_t c = __shfl_sync(0xffffffffu, incl, e + sft - 1);
+        if (c <= q) e += sft;
+    }
+    return e;
 }
 
 // Lanes of the warp whose BITS-bit digit equals this lane's: one ballot per
@@ -252,12 +265,13 @@ __device__ uint32_t lookback_scalar(uint32_t *state, uint32_t part, uint32_t agg
     return excl;
 }
 
-// Decoupled look-back of one digit of a Onesweep pass (one thread per
-// digit): sums the published counts of this digit in the partitions before
-// `part` (kLookWindow per load round) until one with an inclusive prefix.
-// A predecessor that has published nothing is re-read after a short sleep,
-// at most `limit` times; then GS_ERR_TIMEOUT is raised and what was summed
-// is returned.
+// Decoupled look-back of one digit (one thread per digit): sums the
+// published counts of digit d in the partitions before `part` (state row
+// stride R, kLookWindow per load round) until one with an inclusive prefix.
+// The first partition of every segment publishes an inclusive prefix, so the
+// walk never leaves the segment. A predecessor that has published nothing is
+// re-read after a short sleep, at most `limit` times; then GS_ERR_TIMEOUT is
+// raised and what was summed is returned.
 __device__ uint32_t lookback_digit(const uint32_t *state, uint32_t part, int R, int d, uint32_t *err,
                                    int limit)
 {
@@ -296,7 +310,25 @@ __device__ uint32_t lookback_digit(const uint32_t *state, uint32_t part, int R, 
     return excl;
 }
 
-// Block-wide exclusive scan of one value per thread (blockDim.x == 256).
+// Publishes digit d's count of partition `part` (chunk > 0: of a segment
+// that began in an earlier partition) and returns the digit's exclusive
+// prefix within the segment.
+__device__ __forceinline__ uint32_t publish_digit(uint32_t *state, uint32_t part, uint32_t chunk, int R, int d,
+                                                  uint32_t agg, uint32_t *err)
+{
+    uint32_t *st = state + (size_t)part * R + d;
+    if (chunk == 0) {
+        st_relaxed(st, kFlagIncl | agg);
+        return 0;
+    }
+    st_relaxed(st, kFlagAgg | agg);
+    const uint32_t excl = lookback_digit(state, part, R, d, err, kSpinLimit);
+    st_relaxed(st, kFlagIncl | sat_add(excl, agg));
+    return excl;
+}
+
+// Block-wide exclusive scan of one value per thread (WARPS warps).
+template <int WARPS>
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp, uint32_t &total)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -305,7 +337,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp
     __syncthreads();
     uint32_t wex = 0, tot = 0;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) {
+    for (int w = 0; w < WARPS; ++w) {
         const uint32_t t = s_warp[w];
         wex += (w < warp) ? t : 0u;
         tot += t;
@@ -314,27 +346,48 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp
     return wex + x - v;
 }
 
-// 1. compaction of drawn records, index order preserved, plus the histograms
-// of the four depth digits. Lane l of warp w holds records
-// base + (kCompactTile / 8) w + 4 (32 j + l) + e, e < 4, j < kCompactVec
-// (uint4 loads).
+// Row-difference slot of camera c, tile row y (y == tiles_y: the padding row).
+__device__ __forceinline__ uint32_t *rowdiff_at(const BinPlan &bp, uint32_t *rowdiff, int c, int y)
+{
+    return rowdiff + bp.cam[c].gpad + y;
+}
+
+// 1. compaction of drawn records, index order preserved. Lane l of warp w
+// holds records base + (kCompactTile / 8) w + 4 (32 j + l) + e, e < 4,
+// j < kCompactVec (uint4 loads). Also: seg[c] = drawn records before camera
+// c's first record (seg[ncam] = all drawn records); per camera the
+// histograms of the four depth digits (hist[c][pass][256]) and the row
+// difference array (+1 at the first covered row, -1 after the last); the
+// sum of the tile counts. A partition holds records of camera c0 (its first
+// record's) and usually c0 + 1, counted in shared memory; records of other
+// cameras (only when P < kCompactTile) go to global memory directly.
 __global__ void __launch_bounds__(256)
-compact_kernel(const uint32_t *__restrict__ tiles, const uint32_t *__restrict__ dkey, uint32_t N,
+compact_kernel(const __grid_constant__ BinPlan bp, const uint32_t *__restrict__ tiles,
+               const uint32_t *__restrict__ dkey, const ushort4 *__restrict__ rects, uint32_t N,
                uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, WsHeader *hdr,
-               uint32_t *state, uint32_t *__restrict__ hist)
+               uint32_t *state, uint32_t *__restrict__ hist, uint32_t *__restrict__ rowdiff,
+               uint32_t *__restrict__ seg)
 {
     __shared__ uint32_t s_part, s_excl, s_warp[8];
-    __shared__ uint32_t s_h[4][256];
-    for (int i = threadIdx.x; i < 4 * 256; i += 256) (&s_h[0][0])[i] = 0;
+    __shared__ uint32_t s_h[2][4][256];
+    __shared__ uint32_t s_rd[2][kMaxDigits + 1];
+    __shared__ unsigned long long s_k[8];
     if (threadIdx.x == 0) s_part = atomicAdd(&hdr->ctr[CTR_COMPACT], 1u);
     __syncthreads();
     const uint32_t part = s_part;
     const uint32_t nparts = (N + kCompactTile - 1) / kCompactTile;
     if (part >= nparts) return;
+    const uint32_t c0 = bp.pdiv.div(part * kCompactTile);
+    const int nrd0 = bp.cam[c0].tiles_y + 1;
+    const int nrd1 = (int)c0 + 1 < bp.ncam ? bp.cam[c0 + 1].tiles_y + 1 : 0;
+    for (int i = threadIdx.x; i < 2 * 4 * 256; i += 256) (&s_h[0][0][0])[i] = 0;
+    for (int i = threadIdx.x; i < nrd0; i += 256) s_rd[0][i] = 0;
+    for (int i = threadIdx.x; i < nrd1; i += 256) s_rd[1][i] = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t wbase = part * kCompactTile + warp * (kCompactTile / 8);
     uint32_t flags[kCompactVec], incl[kCompactVec], off[kCompactVec];
     uint32_t running = 0;
+    unsigned long long ksum = 0;
 #pragma unroll
     for (int j = 0; j < kCompactVec; ++j) {
         const uint32_t e0 = wbase + 4 * (32 * j + lane);
@@ -342,10 +395,14 @@ compact_kernel(const uint32_t *__restrict__ tiles, const uint32_t *__restrict__ 
         if (e0 + 3 < N) {
             const uint4 t4 = reinterpret_cast<const uint4 *>(tiles)[e0 / 4];
             f = (t4.x > 0) | (t4.y > 0) << 1 | (t4.z > 0) << 2 | (t4.w > 0) << 3;
+            ksum += (unsigned long long)t4.x + t4.y + t4.z + t4.w;
         } else {
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (e0 + e < N && tiles[e0 + e] > 0) f |= 1u << e;
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t t = e0 + e < N ? tiles[e0 + e] : 0u;
+                if (t > 0) f |= 1u << e;
+                ksum += t;
+            }
         }
         flags[j] = f;
         const uint32_t x = warp_incl_scan(__popc(f));
@@ -353,7 +410,12 @@ compact_kernel(const uint32_t *__restrict__ tiles, const uint32_t *__restrict__ 
         off[j] = running;
         running += __shfl_sync(0xffffffffu, x, 31);
     }
-    if (lane == 0) s_warp[warp] = running;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ksum += __shfl_xor_sync(0xffffffffu, ksum, o);
+    if (lane == 0) {
+        s_warp[warp] = running;
+        s_k[warp] = ksum;
+    }
     __syncthreads();
     uint32_t warp_excl = 0, total = 0;
 #pragma unroll
@@ -364,7 +426,12 @@ compact_kernel(const uint32_t *__restrict__ tiles, const uint32_t *__restrict__ 
     }
     if (threadIdx.x < 32) {
         const uint32_t e = lookback_scalar(state, part, total, &hdr->err);
-        if (threadIdx.x == 0) s_excl = e;
+        if (threadIdx.x == 0) {
+            s_excl = e;
+            unsigned long long k = 0;
+            for (int w = 0; w < 8; ++w) k += s_k[w];
+            if (k) atomicAdd(&hdr->k_total, k);
+        }
     }
     __syncthreads();
     const uint32_t excl = s_excl;
@@ -374,40 +441,148 @@ compact_kernel(const uint32_t *__restrict__ tiles, const uint32_t *__restrict__ 
         const uint32_t e0 = wbase + 4 * (32 * j + lane);
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
+            const uint32_t i = e0 + e;
+            if (i >= N) continue;
+            const uint32_t c = bp.pdiv.div(i);
+            if (c * bp.P == i) seg[c] = pos; // first record of camera c
             if (flags[j] >> e & 1u) {
-                const uint32_t key = dkey[e0 + e];
+                const uint32_t key = dkey[i];
+                const ushort4 r = rects[i];
                 if (pos < N) { // always true unless a look-back wait timed out
                     keys_out[pos] = key;
-                    vals_out[pos] = e0 + e;
+                    vals_out[pos] = i;
                 }
                 ++pos;
+                const uint32_t slot = c - c0;
+                if (slot < 2) {
 #pragma unroll
-                for (int p = 0; p < 4; ++p) atomicAdd(&s_h[p][(key >> (8 * p)) & 255u], 1u);
+                    for (int p = 0; p < 4; ++p) atomicAdd(&s_h[slot][p][(key >> (8 * p)) & 255u], 1u);
+                    atomicAdd(&s_rd[slot][r.y], 1u);
+                    atomicAdd(&s_rd[slot][r.w + 1], 0xffffffffu);
+                } else {
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) atomicAdd(&hist[(c * 4 + p) * 256 + ((key >> (8 * p)) & 255u)], 1u);
+                    atomicAdd(rowdiff_at(bp, rowdiff, c, r.y), 1u);
+                    atomicAdd(rowdiff_at(bp, rowdiff, c, r.w + 1), 0xffffffffu);
+                }
             }
         }
     }
-    if (part == nparts - 1 && threadIdx.x == 0) hdr->n_vis = sat_add(excl, total);
+    if (part == nparts - 1 && threadIdx.x == 0) seg[bp.ncam] = sat_add(excl, total);
     __syncthreads();
-    for (int i = threadIdx.x; i < 4 * 256; i += 256) {
-        const uint32_t v = (&s_h[0][0])[i];
-        if (v) atomicAdd(&hist[(i >> 8) * kHistSlot + (i & 255)], v);
+    for (int i = threadIdx.x; i < 2 * 4 * 256; i += 256) {
+        const uint32_t slot = i >> 10;
+        const uint32_t v = (&s_h[0][0][0])[i];
+        if (v && c0 + slot < (uint32_t)bp.ncam) atomicAdd(&hist[(c0 + slot) * 1024 + (i & 1023)], v);
+    }
+    for (int i = threadIdx.x; i < nrd0; i += 256)
+        if (s_rd[0][i]) atomicAdd(rowdiff_at(bp, rowdiff, c0, i), s_rd[0][i]);
+    for (int i = threadIdx.x; i < nrd1; i += 256)
+        if (s_rd[1][i]) atomicAdd(rowdiff_at(bp, rowdiff, c0 + 1, i), s_rd[1][i]);
+}
+
+// 2. plan (one CTA of 1024 threads): record partitions per camera (kSortTile
+// records each: rec_parts[p] = (camera, chunk)); span count of every padded
+// row (the inclusive prefix of the row differences: each camera's block sums
+// to zero, so the prefix restarts at every camera) and its first span
+// (rowbase, exclusive prefix over all rows); span partitions per row
+// (kColTile spans each: span_parts[q] = (row | camera << 18, chunk)); the
+// overlap totals and the capacity check.
+__global__ void __launch_bounds__(1024)
+plan_kernel(const __grid_constant__ BinPlan bp, WsHeader *hdr, const uint32_t *__restrict__ seg,
+            uint2 *__restrict__ rec_parts, uint32_t max_rec_parts, const uint32_t *__restrict__ rowdiff,
+            uint32_t *__restrict__ rowbase, uint2 *__restrict__ span_parts, uint32_t max_span_parts,
+            uint32_t span_cap, uint32_t capacity, int ell)
+{
+    __shared__ uint32_t s_cum[kMaxCams + 1];
+    __shared__ uint32_t s_warp[32];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        uint32_t acc = 0;
+        for (int c = 0; c < bp.ncam; ++c) {
+            s_cum[c] = acc;
+            acc += (seg[c + 1] - seg[c] + kSortTile - 1) / kSortTile;
+        }
+        s_cum[bp.ncam] = acc;
+        hdr->n_rec_parts = min(acc, max_rec_parts);
+        hdr->n_vis = seg[bp.ncam];
+    }
+    __syncthreads();
+    const uint32_t nrp = min(s_cum[bp.ncam], max_rec_parts);
+    for (uint32_t p = tid; p < nrp; p += 1024) {
+        int c = 0;
+        while (c + 1 < bp.ncam && s_cum[c + 1] <= p) ++c;
+        rec_parts[p] = make_uint2((uint32_t)c, p - s_cum[c]);
+    }
+    // rows: thread t owns padded rows [g0, g1)
+    const int G = bp.G;
+    const int per = (G + 1023) / 1024;
+    const int g0 = min(G, tid * per), g1 = min(G, g0 + per);
+    uint32_t dsum = 0;
+    for (int g = g0; g < g1; ++g) dsum += rowdiff[g];
+    uint32_t tot;
+    uint32_t run = block_excl_scan<32>(dsum, s_warp, tot);
+    uint32_t csum = 0;
+    for (int g = g0; g < g1; ++g) {
+        run += rowdiff[g];
+        rowbase[g] = run; // span count of row g, for now
+        csum += run;
+    }
+    __syncthreads();
+    uint32_t R;
+    uint32_t acc = block_excl_scan<32>(csum, s_warp, R);
+    uint32_t nq = 0;
+    for (int g = g0; g < g1; ++g) {
+        const uint32_t cnt = rowbase[g];
+        const uint32_t lo = min(acc, span_cap), hi = min(acc + cnt, span_cap);
+        rowbase[g] = acc;
+        acc += cnt;
+        nq += (hi - lo + kColTile - 1) / kColTile;
+    }
+    if (tid == 1023) rowbase[G] = R;
+    __syncthreads();
+    uint32_t NQ;
+    uint32_t q = block_excl_scan<32>(nq, s_warp, NQ);
+    int c = 0;
+    for (int g = g0; g < g1; ++g) {
+        while (c + 1 < bp.ncam && bp.cam[c + 1].gpad <= g) ++c;
+        const uint32_t lo = min(rowbase[g], span_cap);
+        const uint32_t hi = min(g + 1 == G ? R : rowbase[g + 1], span_cap);
+        const uint32_t n = (hi - lo + kColTile - 1) / kColTile;
+        for (uint32_t k = 0; k < n; ++k, ++q)
+            if (q < max_span_parts) span_parts[q] = make_uint2((uint32_t)g | ((uint32_t)c << 18), k);
+    }
+    if (tid == 0) {
+        hdr->n_span = R;
+        hdr->n_span_parts = min(NQ, max_span_parts);
+        unsigned long long raw = hdr->k_total;
+        if (ell && (unsigned long long)R > raw) raw = R; // empty spans of rows the ellipse misses
+        const uint32_t raw32 = raw >= kValMask ? kValMask : (uint32_t)raw;
+        hdr->n_over_raw = raw32;
+        hdr->n_over = min(raw32, capacity);
+        if (raw > capacity || raw >= kValMask || R > span_cap) atomicOr(&hdr->err, (uint32_t)GS_ERR_CAPACITY);
     }
 }
 
-// One Onesweep pass over BITS bits starting at `shift`. Dynamic shared
-// memory: keys, values, per-warp digit counters, two per-digit tables.
+// One Onesweep pass over BITS bits starting at `shift`, over segments: the
+// keys of segment c are [seg[c], seg[c+1]); partition p covers chunk k of
+// segment c, (c, k) = parts[p] (parts == NULL: one segment, chunk p). Keys
+// move only within their segment. hist + c * hist_stride holds the
+// segment's counts of this pass's digits. Dynamic shared memory: keys,
+// values, per-warp digit counters, two per-digit tables.
 template <int BITS>
 constexpr size_t onesweep_smem()
 {
-    return sizeof(uint32_t) * (2 * kSortTile + 8 * (1 << BITS) + 2 * (1 << BITS) + 8 + 1);
+    return sizeof(uint32_t) * (2 * kSortTile + 8 * (1 << BITS) + 2 * (1 << BITS) + 8 + 4);
 }
 
 template <int BITS>
 __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) // the pass is latency-bound
 onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                 uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
-                const uint32_t *n_ptr, int shift, const uint32_t *__restrict__ hist,
-                uint32_t *state, uint32_t *ctr, uint32_t *err)
+                const uint32_t *__restrict__ seg, const uint2 *__restrict__ parts, const uint32_t *nparts_ptr,
+                int shift, const uint32_t *__restrict__ hist, int hist_stride, uint32_t *state, uint32_t *ctr,
+                uint32_t *err)
 {
     constexpr int R = 1 << BITS;
     constexpr uint32_t M = R - 1;
@@ -425,26 +600,31 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
     if (tid == 0) *s_part = atomicAdd(ctr, 1u);
     for (int i = tid; i < 8 * R; i += kSortThreads) s_whist[i] = 0;
     __syncthreads();
-    const uint32_t n = *n_ptr;
     const uint32_t part = *s_part;
-    const uint32_t nparts = (n + kSortTile - 1) / kSortTile;
+    const uint32_t nparts = parts ? *nparts_ptr : (seg[1] - seg[0] + kSortTile - 1) / kSortTile;
     if (part >= nparts) return;
+    const uint2 pc = parts ? parts[part] : make_uint2(0u, part);
+    const uint32_t c = pc.x, chunk = pc.y;
+    const uint32_t sbeg = seg[c], send = seg[c + 1];
+    const uint32_t beg = sbeg + chunk * kSortTile;
+    const uint32_t end = min(send, beg + kSortTile);
 
-    // warp-striped load: warp w owns keys [base + 32 I w, base + 32 I (w + 1)), I = kSortItems
-    const uint32_t wbase = part * kSortTile + warp * (32 * kSortItems);
+    // warp-striped load: warp w owns keys [beg + 32 I w, beg + 32 I (w + 1)), I = kSortItems
+    const uint32_t wbase = beg + warp * (32 * kSortItems);
     uint32_t k[kSortItems], v[kSortItems], r[kSortItems];
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
         const uint32_t idx = wbase + j * 32 + lane;
-        const bool ok = idx < n;
+        const bool ok = idx < end;
         k[j] = ok ? keys_in[idx] : 0xffffffffu; // invalid keys rank last (top digit, highest index)
         v[j] = ok ? vals_in[idx] : 0u;
     }
-    // this thread's digits' global counts, loaded now so that the latency
+    // this thread's digits' segment counts, loaded now so that the latency
     // overlaps the ranking
+    const uint32_t *hseg = hist + (size_t)c * hist_stride;
     uint32_t hv[DPT];
 #pragma unroll
-    for (int q = 0; q < DPT; ++q) hv[q] = hist[tid * DPT + q];
+    for (int q = 0; q < DPT; ++q) hv[q] = hseg[tid * DPT + q];
     // rank within the warp: match lanes with equal digits
     const uint32_t lt = lanemask_lt();
     uint32_t *wh = s_whist + warp * R;
@@ -468,39 +648,31 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
 #pragma unroll
     for (int q = 0; q < DPT; ++q) {
         const int d = tid * DPT + q;
-        uint32_t c = 0;
+        uint32_t cc = 0;
 #pragma unroll
         for (int w = 0; w < 8; ++w) {
             const uint32_t x = s_whist[w * R + d];
-            s_whist[w * R + d] = c;
-            c += x;
+            s_whist[w * R + d] = cc;
+            cc += x;
         }
-        cnt[q] = c;
-        csum += c;
+        cnt[q] = cc;
+        csum += cc;
         hsum += hv[q];
     }
     uint32_t tot;
-    uint32_t bex = block_excl_scan(csum, s_warp, tot);
+    uint32_t bex = block_excl_scan<8>(csum, s_warp, tot);
     __syncthreads();
-    uint32_t hex = block_excl_scan(hsum, s_warp, tot);
-    // invalid keys exist only in the last partition, all with the top digit
-    const uint32_t last_valid = n - part * kSortTile;
-    const uint32_t n_invalid = last_valid < (uint32_t)kSortTile ? kSortTile - last_valid : 0u;
-    uint32_t *st = state + (size_t)part * R;
+    uint32_t hex = sbeg + block_excl_scan<8>(hsum, s_warp, tot);
+    // invalid keys exist only in a segment's last partition, all with the top digit
+    const uint32_t n_here = end > beg ? end - beg : 0u;
+    const uint32_t n_invalid = kSortTile - n_here;
 #pragma unroll
     for (int q = 0; q < DPT; ++q) {
         const int d = tid * DPT + q;
         s_bexcl[d] = bex;
         bex += cnt[q];
         const uint32_t agg = cnt[q] - (d == (int)M ? n_invalid : 0u);
-        uint32_t excl = 0;
-        if (part == 0) {
-            st_relaxed(&st[d], kFlagIncl | agg);
-        } else {
-            st_relaxed(&st[d], kFlagAgg | agg);
-            excl = lookback_digit(state, part, R, d, err, kSpinLimit);
-            st_relaxed(&st[d], kFlagIncl | sat_add(excl, agg));
-        }
+        const uint32_t excl = publish_digit(state, part, chunk, R, d, agg, err);
         s_goff[d] = hex + excl;
         hex += hv[q];
     }
@@ -514,326 +686,482 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
         s_vals[lp] = v[j];
     }
     __syncthreads();
-    const uint32_t nvalid = min(last_valid, (uint32_t)kSortTile);
-    for (uint32_t i = tid; i < nvalid; i += kSortThreads) {
+    for (uint32_t i = tid; i < n_here; i += kSortThreads) {
         const uint32_t key = s_keys[i];
         const uint32_t d = (key >> shift) & M;
         const uint32_t o = s_goff[d] + i - s_bexcl[d];
-        if (o < n) { // always true unless a look-back wait timed out
+        if (o < send) { // always true unless a look-back wait timed out
             keys_out[o] = key;
             vals_out[o] = s_vals[i];
         }
     }
 }
 
-// 3. overlap emission in depth order, plus the tile-digit histograms. ELL:
-// only the tiles of each rectangle row that the support ellipse reaches
-// (GS_RECT_ELLIPSE), else the whole rectangle.
+// Shared-memory words of the split kernels: per warp a counter per digit
+// (D = max digits + 1 slots), plus the partition id.
+inline size_t split_smem(int max_digits) { return sizeof(uint32_t) * (8 * (size_t)(max_digits + 1) + 4); }
+
+// 4. row split. Partition p = chunk k of camera c's depth-sorted records
+// (the depth sort's partition table). Warp w takes records
+// [beg + 32 I w, beg + 32 I (w + 1)), I = kRowItems, and expands them in
+// order into one span per covered tile row; a span's place is its row's
+// first span (rowbase) + the counts of that row in the camera's earlier
+// partitions (look-back) + in earlier warps of this partition + earlier in
+// this warp. Span = (record index, first column | last column << 16); a row
+// the ellipse misses (GS_RECT_ELLIPSE) gets an empty span (first > last).
 template <bool ELL>
-__global__ void GS_EMIT_BOUNDS
-emit_kernel(const __grid_constant__ CamTable cams, FastDiv pdiv, uint32_t n_records,
-            const uint32_t *__restrict__ sorted_vals,
-            const uint32_t *__restrict__ tiles, const ushort4 *__restrict__ rects,
-            const float4 *__restrict__ rec, int tile_w, int tile_h,
-            uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, uint32_t capacity,
-            WsHeader *hdr, uint32_t *state, TilePlan plan, uint32_t *__restrict__ hist)
+__global__ void __launch_bounds__(256)
+rows_kernel(const __grid_constant__ BinPlan bp, const uint32_t *__restrict__ seg, const uint2 *__restrict__ parts,
+            const WsHeader *hdr, const uint32_t *__restrict__ ids, const ushort4 *__restrict__ rects,
+            const float4 *__restrict__ rec, uint32_t N, const uint32_t *__restrict__ rowbase,
+            uint2 *__restrict__ spans, uint32_t span_cap, uint32_t *state, uint32_t *ctr, uint32_t *err)
 {
-    __shared__ uint32_t s_part, s_excl, s_warp[8];
-    __shared__ uint32_t s_h[3][kHistSlot];
-    __shared__ uint32_t s_tb[kMaxCams], s_tx[kMaxCams]; // per camera: first tile id, tiles per row
-    for (int i = threadIdx.x; i < 3 * kHistSlot; i += 256) (&s_h[0][0])[i] = 0;
-    if (threadIdx.x < cams.ncam) {
-        s_tb[threadIdx.x] = (uint32_t)cams.cam[threadIdx.x].tile_base;
-        s_tx[threadIdx.x] = (uint32_t)cams.cam[threadIdx.x].tiles_x;
-    }
-    if (threadIdx.x == 0) s_part = atomicAdd(&hdr->ctr[CTR_EMIT], 1u);
-    __syncthreads();
-    const uint32_t nv = hdr->n_vis;
-    const uint32_t part = s_part;
-    const uint32_t nparts = (nv + kEmitTile - 1) / kEmitTile;
-    if (part >= nparts) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // warp-striped: item j of lane l is record wbase + 32 j + l (depth order)
-    const uint32_t wbase = part * kEmitTile + warp * (32 * kEmitItems);
-    uint32_t v[kEmitItems], cnt[kEmitItems], incl[kEmitItems], off[kEmitItems];
-    ushort4 rc[kEmitItems];
-    uint32_t running = 0;
-#pragma unroll
-    for (int j = 0; j < kEmitItems; ++j) {
-        const uint32_t idx = wbase + 32 * j + lane;
-        uint32_t vv = idx < nv ? sorted_vals[idx] : 0u;
-        const bool valid = idx < nv && vv < n_records; // ids are < n_records unless a wait timed out
-        if (!valid) vv = 0u;
-        v[j] = vv;
-        rc[j] = valid ? rects[vv] : make_ushort4(0, 0, 0, 0);
-        // a drawn record's rectangle holds exactly its tiles unless rows are
-        // cut to the ellipse: one gather per record instead of two
-        if (ELL)
-            cnt[j] = valid ? tiles[vv] : 0u;
-        else
-            cnt[j] = valid ? ((uint32_t)rc[j].z - rc[j].x + 1u) * ((uint32_t)rc[j].w - rc[j].y + 1u) : 0u;
-        const uint32_t x = warp_incl_scan(cnt[j]);
-        incl[j] = x;
-        off[j] = running;
-        running += __shfl_sync(0xffffffffu, x, 31);
-    }
-    if (lane == 0) s_warp[warp] = running;
-    __syncthreads();
-    uint32_t warp_excl = 0, total = 0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) {
-        const uint32_t t = s_warp[w];
-        warp_excl += (w < warp) ? t : 0u;
-        total += t;
-    }
-    if (threadIdx.x < 32) {
-        const uint32_t e = lookback_scalar(state, part, total, &hdr->err);
-        if (threadIdx.x == 0) s_excl = e;
-    }
-    __syncthreads();
-    const uint32_t part_excl = s_excl;
-    if (ELL) {
-        // two levels: the warp expands its records into tile rows (32 rows at
-        // a time), each lane finds its row's tile columns, then the warp
-        // writes those rows' tiles 32 at a time
-#pragma unroll 1
-        for (int j = 0; j < kEmitItems; ++j) {
-            const uint32_t rows = cnt[j] ? (uint32_t)(rc[j].w - rc[j].y + 1) : 0u;
-            const uint32_t r_incl = warp_incl_scan(rows);
-            const uint32_t r_total = __shfl_sync(0xffffffffu, r_incl, 31);
-            const uint32_t out_base = part_excl + warp_excl + off[j];
-            uint32_t emitted = 0;
-            for (uint32_t rb = 0; rb < r_total; rb += 32) {
-                const uint32_t r = rb + lane;
-                const uint32_t rq = min(r, r_total - 1u);
-                int e = 0;
-#pragma unroll
-                for (int sft = 16; sft > 0; sft >>= 1) {
-                    const uint32_t c = __shfl_sync(0xffffffffu, r_incl, e + sft - 1);
-                    if (c <= rq) e += sft;
+    extern __shared__ uint32_t smem[];
+    const int D = bp.max_ty + 1;
+    uint32_t *s_cnt = smem; // [8][D]
+    uint32_t *s_part = smem + 8 * D;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = lanemask_lt();
+    const uint32_t nparts = hdr->n_rec_parts;
+    uint32_t *wc = s_cnt + warp * D;
+    while (true) {
+        for (int i = tid; i < 8 * D; i += 256) s_cnt[i] = 0;
+        if (tid == 0) *s_part = atomicAdd(ctr, 1u);
+        __syncthreads();
+        const uint32_t part = *s_part;
+        if (part >= nparts) break;
+        const uint2 pc = parts[part];
+        const int c = (int)pc.x;
+        const uint32_t chunk = pc.y;
+        const uint32_t beg = seg[c] + chunk * kRowTile, end = min(seg[c + 1], beg + kRowTile);
+        const int ty = bp.cam[c].tiles_y, tx = bp.cam[c].tiles_x;
+        const uint32_t wb = beg + warp * (32 * kRowItems);
+        // a drawn record's rectangle lies inside its camera's tile grid; the
+        // checks only matter after a timed-out wait left stale entries
+        auto usable = [&](uint32_t id, ushort4 r) {
+            return id < N && r.y <= r.w && r.w < ty && r.x <= r.z && r.z < tx;
+        };
+        // per-warp row counts as a difference array
+#pragma unroll 4
+        for (int j = 0; j < kRowItems; ++j) {
+            const uint32_t idx = wb + 32 * j + lane;
+            if (idx < end) {
+                const uint32_t id = ids[idx];
+                const ushort4 r = id < N ? rects[id] : make_ushort4(1, 1, 0, 0);
+                if (usable(id, r)) {
+                    atomicAdd(&wc[r.y], 1u);
+                    atomicAdd(&wc[r.w + 1], 0xffffffffu);
                 }
-                const uint32_t ev = __shfl_sync(0xffffffffu, v[j], e);
-                const uint32_t rexcl = __shfl_sync(0xffffffffu, r_incl - rows, e);
-                uint32_t cnt2 = 0, kb = 0;
-                if (r < r_total) {
-                    const float4 g0 = rec[3 * (size_t)ev], g1 = rec[3 * (size_t)ev + 1];
-                    const ushort4 rr = rects[ev];
-                    const CamDev &cm = cams.cam[pdiv.div(ev)];
-                    const int ty = (int)rr.y + (int)(rq - rexcl);
-                    int c0 = rr.x, c1 = rr.z;
-                    // a single-row or single-column rectangle keeps all its tiles
-                    const bool simple = rr.z == rr.x || rr.w == rr.y;
-                    if (simple || row_cols(g0.x, g0.y, g1.x, g1.y, g1.z, g1.w, ty, tile_w, tile_h, cm.W,
-                                           cm.H, rr.x, rr.z, c0, c1)) {
-                        cnt2 = (uint32_t)(c1 - c0 + 1);
-                        kb = (uint32_t)cm.tile_base + (uint32_t)ty * cm.tiles_x + (uint32_t)c0;
-                    }
-                }
-                const uint32_t c_incl = warp_incl_scan(cnt2);
-                const uint32_t seg = __shfl_sync(0xffffffffu, c_incl, 31);
-                for (uint32_t b2 = 0; b2 < seg; b2 += 32) {
-                    const uint32_t p = b2 + lane;
-                    const uint32_t pq = min(p, seg - 1u);
-                    int f = 0;
-#pragma unroll
-                    for (int sft = 16; sft > 0; sft >>= 1) {
-                        const uint32_t c = __shfl_sync(0xffffffffu, c_incl, f + sft - 1);
-                        if (c <= pq) f += sft;
-                    }
-                    const uint32_t fkb = __shfl_sync(0xffffffffu, kb, f);
-                    const uint32_t fbeg = __shfl_sync(0xffffffffu, c_incl - cnt2, f);
-                    const uint32_t fv = __shfl_sync(0xffffffffu, ev, f);
-                    const uint32_t o = out_base + emitted + p;
-                    if (p < seg && o < capacity) {
-                        const uint32_t key = fkb + (pq - fbeg);
-                        keys_out[o] = key;
-                        vals_out[o] = fv;
-                        for (int q = 0; q < plan.passes; ++q)
-                            atomicAdd(&s_h[q][(key >> plan.shift[q]) & ((1u << plan.bits[q]) - 1u)], 1u);
-                    }
-                }
-                emitted += seg;
             }
         }
-    }
-#pragma unroll
-    for (int j = 0; j < (ELL ? 0 : kEmitItems); ++j) {
-        const uint32_t w_incl = incl[j];
-        const uint32_t w_total = __shfl_sync(0xffffffffu, w_incl, 31);
-        const uint32_t out_base = part_excl + warp_excl + off[j];
-        const uint32_t cam = pdiv.div(v[j]);
-        const uint32_t tiles_x = s_tx[cam];
-        const uint32_t tbase = s_tb[cam] + (uint32_t)rc[j].y * tiles_x + rc[j].x;
-        const uint32_t rw = (uint32_t)rc[j].z - rc[j].x + 1u;
-        const float rrw = 1.f / (float)rw;
-        const uint32_t beg = w_incl - cnt[j];
-        // the warp walks these overlaps 32 at a time; every lane takes part
-        // in every shuffle, lanes past the end only skip the store
-        for (uint32_t b = 0; b < w_total; b += 32) {
-            const uint32_t p = b + lane;
-            const uint32_t pq = min(p, w_total - 1u);
-            int e = 0; // owner lane: number of lanes whose inclusive prefix is <= pq
-#pragma unroll
-            for (int sft = 16; sft > 0; sft >>= 1) {
-                const uint32_t c = __shfl_sync(0xffffffffu, w_incl, e + sft - 1);
-                if (c <= pq) e += sft;
-            }
-            const uint32_t ev = __shfl_sync(0xffffffffu, v[j], e);
-            const uint32_t ebeg = __shfl_sync(0xffffffffu, beg, e);
-            const uint32_t erw = __shfl_sync(0xffffffffu, rw, e);
-            const uint32_t etb = __shfl_sync(0xffffffffu, tbase, e);
-            const uint32_t etx = __shfl_sync(0xffffffffu, tiles_x, e);
-            const float errw = __shfl_sync(0xffffffffu, rrw, e);
-            const uint32_t l = pq - ebeg;
-            // l / erw from the reciprocal (l < 2^22: off by at most one), corrected
-            uint32_t row = (uint32_t)((float)l * errw);
-            row -= (row * erw > l) ? 1u : 0u;
-            row += ((row + 1u) * erw <= l) ? 1u : 0u;
-            const uint32_t col = l - row * erw;
-            const uint32_t o = out_base + p;
-            const bool act = p < w_total && o < capacity; // a prefix of the warp's lanes
-            const uint32_t key = etb + row * etx + col;
-            if (act) {
-                keys_out[o] = key;
-                vals_out[o] = ev;
-                atomicAdd(&s_h[0][(key >> plan.shift[0]) & ((1u << plan.bits[0]) - 1u)], 1u);
-            }
-#if GS_EMIT_RUNS
-            // higher digits: consecutive lanes mostly hold consecutive tile
-            // ids with one digit; one atomic per run of equal digits
-            const uint32_t nact = __popc(__ballot_sync(0xffffffffu, act));
-            for (int q = 1; q < plan.passes; ++q) {
-                const uint32_t d = (key >> plan.shift[q]) & ((1u << plan.bits[q]) - 1u);
-                const uint32_t dp = __shfl_up_sync(0xffffffffu, d, 1);
-                const bool head = act && (lane == 0 || dp != d);
-                const uint32_t heads = __ballot_sync(0xffffffffu, head);
-                if (head) {
-                    const uint32_t after = heads & (0xfffffffeu << lane);
-                    const uint32_t next = after ? (uint32_t)(__ffs(after) - 1) : 32u;
-                    atomicAdd(&s_h[q][d], min(next, nact) - (uint32_t)lane);
-                }
-            }
-#else
-            if (act)
-                for (int q = 1; q < plan.passes; ++q)
-                    atomicAdd(&s_h[q][(key >> plan.shift[q]) & ((1u << plan.bits[q]) - 1u)], 1u);
-#endif
+        __syncwarp();
+        uint32_t carry = 0;
+        for (int y0 = 0; y0 < ty; y0 += 32) {
+            const int y = y0 + lane;
+            const uint32_t x = warp_incl_scan(y < ty ? wc[y] : 0u) + carry;
+            if (y < ty) wc[y] = x;
+            carry = __shfl_sync(0xffffffffu, x, 31);
         }
-    }
-    if (part == nparts - 1 && threadIdx.x == 0) {
-        const uint32_t tot = sat_add(part_excl, total);
-        hdr->n_over_raw = tot;
-        hdr->n_over = min(tot, capacity);
-        if (tot > capacity || tot >= kValMask) atomicOr(&hdr->err, (uint32_t)GS_ERR_CAPACITY);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < plan.passes * kHistSlot; i += 256) {
-        const uint32_t x = (&s_h[0][0])[i];
-        if (x) atomicAdd(&hist[i], x);
+        __syncthreads();
+        const int gp = bp.cam[c].gpad;
+        for (int y = tid; y < ty; y += 256) {
+            uint32_t a = 0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                const uint32_t x = s_cnt[w * D + y];
+                s_cnt[w * D + y] = a;
+                a += x;
+            }
+            const uint32_t base = rowbase[gp + y] + publish_digit(state, part, chunk, bp.max_ty, y, a, err);
+#pragma unroll
+            for (int w = 0; w < 8; ++w) s_cnt[w * D + y] += base;
+        }
+        __syncthreads();
+        const int W = bp.cam[c].W, H = bp.cam[c].H;
+        for (int j = 0; j < kRowItems; ++j) {
+            if (wb + 32 * j >= end) break; // uniform per warp
+            const uint32_t idx = wb + 32 * j + lane;
+            uint32_t id = 0, h = 0;
+            ushort4 r = make_ushort4(0, 0, 0, 0);
+            if (idx < end) {
+                id = ids[idx];
+                r = id < N ? rects[id] : make_ushort4(1, 1, 0, 0);
+                if (usable(id, r))
+                    h = (uint32_t)r.w - r.y + 1u;
+                else
+                    r = make_ushort4(0, 0, 0, 0);
+            }
+            const uint32_t incl = warp_incl_scan(h);
+            const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+            const uint32_t xr = (uint32_t)r.x | ((uint32_t)r.z << 16);
+            const uint32_t yr = (uint32_t)r.y | ((uint32_t)r.w << 16);
+            for (uint32_t b = 0; b < tot; b += 32) {
+                const uint32_t p = b + lane;
+                const uint32_t pq = min(p, tot - 1u);
+                const int e = owner_lane(incl, pq);
+                const uint32_t eid = __shfl_sync(0xffffffffu, id, e);
+                const uint32_t exr = __shfl_sync(0xffffffffu, xr, e);
+                const uint32_t eyr = __shfl_sync(0xffffffffu, yr, e);
+                const uint32_t ebeg = __shfl_sync(0xffffffffu, incl - h, e);
+                const bool act = p < tot;
+                const uint32_t y = (eyr & 0xffffu) + (pq - ebeg);
+                uint32_t span_x = exr;
+                if (ELL && act) {
+                    const int x0 = (int)(exr & 0xffffu), x1 = (int)(exr >> 16);
+                    const bool simple = x0 == x1 || (eyr & 0xffffu) == (eyr >> 16);
+                    if (!simple) {
+                        const float4 g0 = rec[3 * (size_t)eid], g1 = rec[3 * (size_t)eid + 1];
+                        int a0, a1;
+                        span_x = row_cols(g0.x, g0.y, g1.x, g1.y, g1.z, g1.w, (int)y, bp.tile_w, bp.tile_h, W, H,
+                                          x0, x1, a0, a1)
+                                     ? ((uint32_t)a0 | ((uint32_t)a1 << 16))
+                                     : 0xffffu;
+                    }
+                }
+                const uint32_t peers = __match_any_sync(0xffffffffu, act ? y : 0x10000u + lane);
+                const int leader = __ffs(peers) - 1;
+                uint32_t base = 0;
+                if (act && lane == leader) {
+                    base = wc[y];
+                    wc[y] = base + __popc(peers);
+                }
+                base = __shfl_sync(0xffffffffu, base, leader);
+                const uint32_t pos = base + __popc(peers & lt);
+                if (act && pos < span_cap) spans[pos] = make_uint2(eid, span_x);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
     }
 }
 
-// 5. per-tile [start, end) and optional 64-bit keys. Each thread takes four
-// consecutive sorted keys (one 16-byte load); the neighbours across thread
-// boundaries come from the adjacent lanes, or from memory at warp edges.
-__global__ void __launch_bounds__(256)
-ranges_kernel(const uint32_t *__restrict__ tkeys, const uint32_t *__restrict__ vals,
-              const uint32_t *__restrict__ dkey, const WsHeader *hdr, uint2 *__restrict__ ranges,
-              unsigned long long *__restrict__ keys64, uint32_t total_tiles, uint32_t n_records)
+// Camera c, tile row y and [beg, end) of span partition `part`.
+struct SpanPart {
+    int c, y;
+    uint32_t chunk, beg, end;
+};
+__device__ __forceinline__ SpanPart span_part(const BinPlan &bp, const uint2 *parts, uint32_t part,
+                                              const uint32_t *rowbase, uint32_t span_cap)
 {
-    const uint32_t n = hdr->n_over;
-    const uint32_t nq = (n + 3) / 4;
-    const int lane = threadIdx.x & 31;
-    const uint32_t stride = gridDim.x * 256;
-    // every lane of a warp runs the same number of rounds (full-mask shuffles)
-    for (uint32_t q0 = blockIdx.x * 256 + (threadIdx.x & ~31u); q0 < nq; q0 += stride) {
-        const uint32_t q = q0 + lane;
-        const uint32_t i0 = 4 * q;
-        uint32_t k[4];
-        if (i0 + 3 < n) {
-            const uint4 t = *reinterpret_cast<const uint4 *>(tkeys + i0);
-            k[0] = t.x, k[1] = t.y, k[2] = t.z, k[3] = t.w;
-        } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) k[e] = i0 + e < n ? tkeys[i0 + e] : 0xffffffffu;
-        }
-        uint32_t prev = __shfl_up_sync(0xffffffffu, k[3], 1);
-        uint32_t next = __shfl_down_sync(0xffffffffu, k[0], 1);
-        if (lane == 0) prev = (i0 > 0 && i0 - 1 < n) ? tkeys[i0 - 1] : 0xfffffffeu;
-        if (lane == 31) next = i0 + 4 < n ? tkeys[i0 + 4] : 0xfffffffeu;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const uint32_t i = i0 + e;
-            const uint32_t t = k[e];
-            if (i >= n || t >= total_tiles) continue; // t >= total_tiles only after a timed-out wait
-            const uint32_t before = e == 0 ? prev : k[e - 1];
-            const uint32_t after = e == 3 ? next : (i + 1 < n ? k[e + 1] : 0xfffffffeu);
-            if (i == 0 || before != t) ranges[t].x = i;
-            if (i + 1 == n || after != t) ranges[t].y = i + 1;
-            if (keys64) {
-                const uint32_t v = vals[i];
-                keys64[i] = ((unsigned long long)t << 32) | (v < n_records ? dkey[v] : 0xffffffffu);
+    const uint2 pc = parts[part];
+    SpanPart s;
+    const int g = (int)(pc.x & 0x3ffffu);
+    s.c = (int)(pc.x >> 18);
+    s.y = g - bp.cam[s.c].gpad;
+    s.chunk = pc.y;
+    const uint32_t lo = min(rowbase[g], span_cap), hi = min(rowbase[g + 1], span_cap);
+    s.beg = lo + s.chunk * kColTile;
+    s.end = min(hi, s.beg + kColTile);
+    return s;
+}
+
+// 5. tile counts: per span partition a difference array over the row's
+// columns, added to the tiles' counters.
+__global__ void __launch_bounds__(256)
+cols_count_kernel(const __grid_constant__ BinPlan bp, const uint2 *__restrict__ parts, const WsHeader *hdr,
+                  const uint32_t *__restrict__ rowbase, const uint2 *__restrict__ spans, uint32_t span_cap,
+                  uint32_t *__restrict__ tile_cnt, uint32_t *ctr)
+{
+    extern __shared__ uint32_t smem[];
+    const int D = bp.max_tx + 1;
+    uint32_t *s_d = smem;
+    uint32_t *s_part = smem + 8 * D;
+    const int tid = threadIdx.x;
+    const uint32_t nparts = hdr->n_span_parts;
+    while (true) {
+        for (int i = tid; i < D; i += 256) s_d[i] = 0;
+        if (tid == 0) *s_part = atomicAdd(ctr, 1u);
+        __syncthreads();
+        const uint32_t part = *s_part;
+        if (part >= nparts) break;
+        const SpanPart sp = span_part(bp, parts, part, rowbase, span_cap);
+        const int tx = bp.cam[sp.c].tiles_x;
+        const uint32_t end = sp.y < bp.cam[sp.c].tiles_y ? sp.end : sp.beg; // the padding row has no spans
+        for (uint32_t i = sp.beg + tid; i < end; i += 256) {
+            const uint32_t xr = spans[i].y;
+            const uint32_t x0 = xr & 0xffffu, x1 = xr >> 16;
+            if (x0 <= x1 && x1 < (uint32_t)tx) {
+                atomicAdd(&s_d[x0], 1u);
+                atomicAdd(&s_d[x1 + 1], 0xffffffffu);
             }
+        }
+        __syncthreads();
+        if (tid < 32) {
+            uint32_t *tc = tile_cnt + bp.cam[sp.c].tile_base + (uint32_t)sp.y * tx;
+            uint32_t carry = 0;
+            for (int x0 = 0; x0 < tx; x0 += 32) {
+                const int x = x0 + tid;
+                const uint32_t v = warp_incl_scan(x < tx ? s_d[x] : 0u) + carry;
+                if (x < tx && v) atomicAdd(&tc[x], v);
+                carry = __shfl_sync(0xffffffffu, v, 31);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// 6. per-tile ranges: exclusive scan of the tile counts (single pass,
+// decoupled look-back), clamped to the capacity; (0, 0) for an empty tile.
+__global__ void __launch_bounds__(256)
+tile_scan_kernel(const uint32_t *__restrict__ tile_cnt, uint32_t T, uint2 *__restrict__ ranges, uint32_t cap,
+                 WsHeader *hdr, uint32_t *state)
+{
+    __shared__ uint32_t s_part, s_excl, s_warp[8];
+    if (threadIdx.x == 0) s_part = atomicAdd(&hdr->ctr[CTR_SCAN], 1u);
+    __syncthreads();
+    const uint32_t part = s_part;
+    const uint32_t t0 = part * kScanTile + threadIdx.x * kScanItems;
+    uint32_t v[kScanItems], sum = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = t0 + i < T ? tile_cnt[t0 + i] : 0u;
+        sum += v[i];
+    }
+    uint32_t tot;
+    uint32_t ex = block_excl_scan<8>(sum, s_warp, tot);
+    if (threadIdx.x < 32) {
+        const uint32_t e = lookback_scalar(state, part, tot, &hdr->err);
+        if (threadIdx.x == 0) s_excl = e;
+    }
+    __syncthreads();
+    uint32_t base = s_excl + ex;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        // an empty tile reads (0, 0), as a zero-filled table would
+        if (t0 + i < T) ranges[t0 + i] = v[i] ? make_uint2(min(base, cap), min(base + v[i], cap)) : make_uint2(0u, 0u);
+        base += v[i];
+    }
+}
+
+// 7. column split. Partition q = chunk k of row (c, y)'s spans. Warp w
+// takes spans [beg + 32 I w, beg + 32 I (w + 1)), I = kColItems, and expands
+// them in order into one entry per covered column; the entry's place is its
+// tile's range start + the counts of that column in the row's earlier
+// partitions (look-back) + in earlier warps + earlier in this warp. Writes
+// the record index there (places at or past the capacity are dropped; the
+// overflow is flagged by the plan).
+__global__ void __launch_bounds__(256)
+cols_kernel(const __grid_constant__ BinPlan bp, const uint2 *__restrict__ parts, const WsHeader *hdr,
+            const uint32_t *__restrict__ rowbase, const uint2 *__restrict__ spans, uint32_t span_cap,
+            const uint2 *__restrict__ ranges, uint32_t *__restrict__ vals, uint32_t cap, uint32_t *state,
+            uint32_t *ctr, uint32_t *err)
+{
+    extern __shared__ uint32_t smem[];
+    const int D = bp.max_tx + 1;
+    uint32_t *s_cnt = smem; // [8][D]
+    uint32_t *s_part = smem + 8 * D;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = lanemask_lt();
+    const uint32_t nparts = hdr->n_span_parts;
+    uint32_t *wc = s_cnt + warp * D;
+    while (true) {
+        for (int i = tid; i < 8 * D; i += 256) s_cnt[i] = 0;
+        if (tid == 0) *s_part = atomicAdd(ctr, 1u);
+        __syncthreads();
+        const uint32_t part = *s_part;
+        if (part >= nparts) break;
+        SpanPart sp = span_part(bp, parts, part, rowbase, span_cap);
+        const int tx = bp.cam[sp.c].tiles_x;
+        if (sp.y >= bp.cam[sp.c].tiles_y) sp.end = sp.beg; // the padding row has no spans
+        const uint32_t wb = sp.beg + warp * (32 * kColItems);
+#pragma unroll 4
+        for (int j = 0; j < kColItems; ++j) {
+            const uint32_t idx = wb + 32 * j + lane;
+            if (idx < sp.end) {
+                const uint32_t xr = spans[idx].y;
+                const uint32_t x0 = xr & 0xffffu, x1 = xr >> 16;
+                if (x0 <= x1 && x1 < (uint32_t)tx) {
+                    atomicAdd(&wc[x0], 1u);
+                    atomicAdd(&wc[x1 + 1], 0xffffffffu);
+                }
+            }
+        }
+        __syncwarp();
+        uint32_t carry = 0;
+        for (int x0 = 0; x0 < tx; x0 += 32) {
+            const int x = x0 + lane;
+            const uint32_t v = warp_incl_scan(x < tx ? wc[x] : 0u) + carry;
+            if (x < tx) wc[x] = v;
+            carry = __shfl_sync(0xffffffffu, v, 31);
+        }
+        __syncthreads();
+        const uint32_t trow = (uint32_t)bp.cam[sp.c].tile_base + (uint32_t)sp.y * tx;
+        for (int x = tid; x < tx; x += 256) {
+            uint32_t a = 0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                const uint32_t v = s_cnt[w * D + x];
+                s_cnt[w * D + x] = a;
+                a += v;
+            }
+            const uint32_t base = ranges[trow + x].x + publish_digit(state, part, sp.chunk, bp.max_tx, x, a, err);
+#pragma unroll
+            for (int w = 0; w < 8; ++w) s_cnt[w * D + x] += base;
+        }
+        __syncthreads();
+        for (int j = 0; j < kColItems; ++j) {
+            if (wb + 32 * j >= sp.end) break; // uniform per warp
+            const uint32_t idx = wb + 32 * j + lane;
+            uint32_t id = 0, n = 0, x0 = 0;
+            if (idx < sp.end) {
+                const uint2 s = spans[idx];
+                id = s.x;
+                x0 = s.y & 0xffffu;
+                const uint32_t x1 = s.y >> 16;
+                n = (x0 <= x1 && x1 < (uint32_t)tx) ? x1 - x0 + 1u : 0u;
+            }
+            const uint32_t incl = warp_incl_scan(n);
+            const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+            for (uint32_t b = 0; b < tot; b += 32) {
+                const uint32_t p = b + lane;
+                const uint32_t pq = min(p, tot - 1u);
+                const int e = owner_lane(incl, pq);
+                const uint32_t eid = __shfl_sync(0xffffffffu, id, e);
+                const uint32_t ex0 = __shfl_sync(0xffffffffu, x0, e);
+                const uint32_t ebeg = __shfl_sync(0xffffffffu, incl - n, e);
+                const bool act = p < tot;
+                const uint32_t x = ex0 + (pq - ebeg);
+                const uint32_t peers = __match_any_sync(0xffffffffu, act ? x : 0x10000u + lane);
+                const int leader = __ffs(peers) - 1;
+                uint32_t base = 0;
+                if (act && lane == leader) {
+                    base = wc[x];
+                    wc[x] = base + __popc(peers);
+                }
+                base = __shfl_sync(0xffffffffu, base, leader);
+                const uint32_t pos = base + __popc(peers & lt);
+                if (act && pos < cap) vals[pos] = eid;
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Optional 64-bit keys of the sorted lists (tile << 32 | depth bits): one
+// warp per tile.
+__global__ void __launch_bounds__(256)
+keys64_kernel(const uint2 *__restrict__ ranges, uint32_t T, const uint32_t *__restrict__ vals,
+              const uint32_t *__restrict__ dkey, uint32_t N, unsigned long long *__restrict__ keys64)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t t = (blockIdx.x * 256 + threadIdx.x) >> 5; t < T; t += gridDim.x * 8) {
+        const uint2 rg = ranges[t];
+        for (uint32_t i = rg.x + lane; i < rg.y; i += 32) {
+            const uint32_t v = vals[i];
+            keys64[i] = ((unsigned long long)t << 32) | (v < N ? dkey[v] : 0xffffffffu);
         }
     }
 }
 
 struct WsLayout {
-    size_t hdr, hist, st_compact, st_depth, st_emit, st_tile, zero_end;
-    size_t dk0, dk1, dv0, dv1, tk0, tk1, tv1, total;
-    uint32_t parts_depth, parts_tile;
-    size_t st_depth_stride, st_tile_stride; // uint32 entries per pass
+    size_t hdr, hist, rowdiff, seg, st_compact, st_depth, st_rows, st_cols, st_scan, tile_cnt, zero_end;
+    size_t rowbase, rec_parts, span_parts, dk0, dk1, dv0, dv1, spans, total;
+    uint32_t max_rec_parts, max_span_parts;
+    size_t st_depth_stride; // uint32 entries per pass
 };
 
-WsLayout ws_layout(int64_t N, int64_t cap, const TilePlan &plan)
+WsLayout ws_layout(const BinPlan &bp, int64_t N, int64_t cap, int64_t total_tiles)
 {
     WsLayout L;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o += align256(bytes); return r; };
-    L.parts_depth = (uint32_t)((N + kSortTile - 1) / kSortTile);
-    L.parts_tile = (uint32_t)((cap + kSortTile - 1) / kSortTile);
-    const int rt = 1 << plan.bits[0];
-    L.st_depth_stride = (size_t)256 * (L.parts_depth + 1);
-    L.st_tile_stride = (size_t)rt * (L.parts_tile + 1);
+    L.max_rec_parts = (uint32_t)((N + kSortTile - 1) / kSortTile + bp.ncam);
+    L.max_span_parts = (uint32_t)((cap + kColTile - 1) / kColTile + bp.G);
+    L.st_depth_stride = (size_t)256 * L.max_rec_parts;
     L.hdr = take(sizeof(WsHeader));
-    L.hist = take(sizeof(uint32_t) * 8 * kHistSlot);
+    L.hist = take(sizeof(uint32_t) * 1024 * bp.ncam);
+    L.rowdiff = take(sizeof(uint32_t) * bp.G);
+    L.seg = take(sizeof(uint32_t) * (bp.ncam + 1));
     L.st_compact = take(sizeof(uint32_t) * ((N + kCompactTile - 1) / kCompactTile + 1));
     L.st_depth = take(sizeof(uint32_t) * 4 * L.st_depth_stride);
-    L.st_emit = take(sizeof(uint32_t) * ((N + kEmitTile - 1) / kEmitTile + 1));
-    L.st_tile = take(sizeof(uint32_t) * plan.passes * L.st_tile_stride);
+    L.st_rows = take(sizeof(uint32_t) * (size_t)bp.max_ty * L.max_rec_parts);
+    L.st_cols = take(sizeof(uint32_t) * (size_t)bp.max_tx * L.max_span_parts);
+    L.st_scan = take(sizeof(uint32_t) * ((total_tiles + kScanTile - 1) / kScanTile + 1));
+    L.tile_cnt = take(sizeof(uint32_t) * total_tiles);
     L.zero_end = o;
+    L.rowbase = take(sizeof(uint32_t) * (bp.G + 1));
+    L.rec_parts = take(sizeof(uint2) * L.max_rec_parts);
+    L.span_parts = take(sizeof(uint2) * L.max_span_parts);
     L.dk0 = take(sizeof(uint32_t) * N + 16);
     L.dk1 = take(sizeof(uint32_t) * N);
     L.dv0 = take(sizeof(uint32_t) * N);
     L.dv1 = take(sizeof(uint32_t) * N);
-    L.tk0 = take(sizeof(uint32_t) * cap);
-    L.tk1 = take(sizeof(uint32_t) * cap);
-    L.tv1 = take(sizeof(uint32_t) * cap);
+    L.spans = take(sizeof(uint2) * cap);
     L.total = o;
     return L;
 }
 
+bool make_bin_plan(const CamTable &t, const gs_config *cfg, int32_t P, BinPlan *bp)
+{
+    bp->ncam = t.ncam;
+    bp->P = (uint32_t)std::max(P, 1);
+    bp->pdiv = FastDiv::make(bp->P);
+    bp->tile_w = cfg->tile_w;
+    bp->tile_h = cfg->tile_h;
+    int g = 0, mx = 1, my = 1;
+    for (int c = 0; c < kMaxCams; ++c) {
+        BinCam &b = bp->cam[c];
+        if (c >= t.ncam) {
+            b = BinCam{0, 0, 0, g, 0, 0};
+            continue;
+        }
+        const CamDev &d = t.cam[c];
+        if (d.tiles_x > kMaxDigits || d.tiles_y > kMaxDigits) return false;
+        b = BinCam{d.tiles_x, d.tiles_y, d.tile_base, g, d.W, d.H};
+        g += d.tiles_y + 1;
+        mx = std::max(mx, d.tiles_x);
+        my = std::max(my, d.tiles_y);
+    }
+    bp->G = g;
+    bp->max_tx = mx;
+    bp->max_ty = my;
+    return true;
+}
+
+// Sets the dynamic shared-memory opt-in of a kernel once per device (so that
+// later calls, e.g. under stream capture, only launch).
+template <typename K>
+cudaError_t smem_optin(K kernel, size_t bytes, bool *done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 64 && done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && dev < 64) done[dev] = true;
+    return e;
+}
+
 template <int BITS>
 cudaError_t launch_onesweep(unsigned grid, cudaStream_t s, const uint32_t *ki, const uint32_t *vi,
-                            uint32_t *ko, uint32_t *vo, const uint32_t *n, int shift,
-                            const uint32_t *hist, uint32_t *state, uint32_t *ctr, uint32_t *err)
+                            uint32_t *ko, uint32_t *vo, const uint32_t *seg, const uint2 *parts,
+                            const uint32_t *nparts, int shift, const uint32_t *hist, int hist_stride,
+                            uint32_t *state, uint32_t *ctr, uint32_t *err)
 {
     const size_t sm = onesweep_smem<BITS>();
-    // the shared-memory opt-in is set once per device (so that later calls,
-    // e.g. under stream capture, only launch)
     static bool attr_set[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return cudaGetLastError();
-    if (dev >= 64 || !attr_set[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<BITS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        if (dev < 64) attr_set[dev] = true;
-    }
-    onesweep_kernel<BITS><<<grid ? grid : 1, kSortThreads, sm, s>>>(ki, vi, ko, vo, n, shift, hist,
-                                                                   state, ctr, err);
+    cudaError_t e = smem_optin(onesweep_kernel<BITS>, sm, attr_set);
+    if (e != cudaSuccess) return e;
+    onesweep_kernel<BITS><<<grid ? grid : 1, kSortThreads, sm, s>>>(ki, vi, ko, vo, seg, parts, nparts, shift,
+                                                                   hist, hist_stride, state, ctr, err);
     count_launch();
     return cudaPeekAtLastError();
+}
+
+// Grid of a persistent split kernel: every SM filled, never more CTAs than
+// partitions can exist.
+unsigned split_grid(uint32_t max_parts)
+{
+    static int sms[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    int n = dev < 64 ? sms[dev] : 0;
+    if (n == 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+        if (dev < 64) sms[dev] = n;
+    }
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)n * GS_SPLIT_BLOCKS, max_parts));
 }
 
 } // namespace
@@ -841,10 +1169,16 @@ cudaError_t launch_onesweep(unsigned grid, cudaStream_t s, const uint32_t *ki, c
 
 using namespace gs;
 
-extern "C" size_t gs_bin_sort_workspace_bytes(int64_t n_records, int64_t capacity, int64_t total_tiles)
+extern "C" size_t gs_bin_sort_workspace_bytes(const gs_camera *cams, int32_t ncam, int32_t P,
+                                              const gs_config *cfg, int64_t capacity)
 {
-    if (n_records < 0 || capacity < 0 || total_tiles < 0) return 0;
-    return ws_layout(n_records, capacity, tile_plan(total_tiles)).total;
+    if (!cams || !cfg || ncam <= 0 || ncam > kMaxCams || P < 0 || capacity < 0) return 0;
+    const int64_t N = (int64_t)ncam * P;
+    if (N >= (int64_t)kValMask || capacity >= (int64_t)kValMask) return 0;
+    CamTable t;
+    BinPlan bp;
+    if (!build_cam_table(cams, ncam, cfg, &t) || !make_bin_plan(t, cfg, P, &bp)) return 0;
+    return ws_layout(bp, N, capacity, t.total_tiles).total;
 }
 
 extern "C" gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t ncam, int32_t P,
@@ -859,32 +1193,44 @@ extern "C" gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t nc
         return GS_ERR_ARG;
     if (N > 0 && (!d_splat2d || ((uintptr_t)d_splat2d & 255))) return GS_ERR_ARG;
     CamTable t;
-    if (!build_cam_table(cams, ncam, cfg, &t)) return GS_ERR_ARG;
-    const TilePlan plan = tile_plan(t.total_tiles);
-    const WsLayout L = ws_layout(N, capacity, plan);
+    BinPlan bp;
+    if (!build_cam_table(cams, ncam, cfg, &t) || !make_bin_plan(t, cfg, P, &bp)) return GS_ERR_ARG;
+    const WsLayout L = ws_layout(bp, N, capacity, t.total_tiles);
     if (workspace_bytes < L.total) return GS_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char *ws = static_cast<char *>(d_workspace);
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws + L.hdr);
-    uint32_t *hist = reinterpret_cast<uint32_t *>(ws + L.hist);
     auto U = [&](size_t off) { return reinterpret_cast<uint32_t *>(ws + off); };
+    auto U2 = [&](size_t off) { return reinterpret_cast<uint2 *>(ws + off); };
+    uint2 *ranges = reinterpret_cast<uint2 *>(d_ranges);
+    const uint32_t T = (uint32_t)t.total_tiles;
+    const uint32_t cap = (uint32_t)capacity;
 
     if (cudaMemsetAsync(ws, 0, L.zero_end, s) != cudaSuccess) return GS_ERR_CUDA;
-    if (cudaMemsetAsync(d_ranges, 0, sizeof(uint32_t) * 2 * (size_t)t.total_tiles, s) != cudaSuccess)
-        return GS_ERR_CUDA;
-    if (N > 0) {
+    if (N == 0) {
+        if (cudaMemsetAsync(d_ranges, 0, sizeof(uint2) * (size_t)T, s) != cudaSuccess) return GS_ERR_CUDA;
+    } else {
+        static bool optin_rows[2][64] = {}, optin_cc[64] = {}, optin_cols[64] = {};
         Splat2DConst sp = splat2d_const(d_splat2d, N);
-        // 1. compaction + depth-digit histograms
+        const bool ell = cfg->rect_mode == GS_RECT_ELLIPSE;
+        // 1. compaction, per-camera histograms and row differences
         compact_kernel<<<(unsigned)((N + kCompactTile - 1) / kCompactTile), 256, 0, s>>>(
-            sp.tiles, sp.dkey, (uint32_t)N, U(L.dk0), U(L.dv0), hdr, U(L.st_compact), hist);
+            bp, sp.tiles, sp.dkey, sp.rect, (uint32_t)N, U(L.dk0), U(L.dv0), hdr, U(L.st_compact), U(L.hist),
+            U(L.rowdiff), U(L.seg));
         count_launch();
         GS_LAUNCH_CHECK();
-        // 2. depth sort, 4 passes ping-pong: result back in (dk0, dv0)
+        // 2. plan
+        plan_kernel<<<1, 1024, 0, s>>>(bp, hdr, U(L.seg), U2(L.rec_parts), L.max_rec_parts, U(L.rowdiff),
+                                       U(L.rowbase), U2(L.span_parts), L.max_span_parts, cap, cap, ell ? 1 : 0);
+        count_launch();
+        GS_LAUNCH_CHECK();
+        // 3. depth sort within each camera, 4 passes ping-pong: result back in (dk0, dv0)
         uint32_t *kin = U(L.dk0), *vin = U(L.dv0), *kout = U(L.dk1), *vout = U(L.dv1);
         for (int p = 0; p < 4; ++p) {
-            if (launch_onesweep<8>(L.parts_depth, s, kin, vin, kout, vout, &hdr->n_vis, 8 * p,
-                                   hist + kHistSlot * p, U(L.st_depth) + p * L.st_depth_stride,
-                                   &hdr->ctr[CTR_DEPTH + p], &hdr->err) != cudaSuccess) {
+            if (launch_onesweep<8>(L.max_rec_parts, s, kin, vin, kout, vout, U(L.seg), U2(L.rec_parts),
+                                   &hdr->n_rec_parts, 8 * p, U(L.hist) + 256 * p, 1024,
+                                   U(L.st_depth) + p * L.st_depth_stride, &hdr->ctr[CTR_DEPTH + p],
+                                   &hdr->err) != cudaSuccess) {
                 cudaGetLastError();
                 return GS_ERR_CUDA;
             }
@@ -892,50 +1238,59 @@ extern "C" gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t nc
             std::swap(vin, vout);
         }
         if (capacity > 0) {
-            // 3. emission into the buffers that make the last tile pass land in d_vals
-            uint32_t *ek = U(L.tk0);
-            uint32_t *ev = (plan.passes % 2 == 0) ? d_vals : U(L.tv1);
-            uint32_t *thist = hist + 4 * kHistSlot;
-            const unsigned eblocks = (unsigned)((N + kEmitTile - 1) / kEmitTile);
-            const FastDiv pdiv = FastDiv::make((uint32_t)std::max(P, 1));
-            if (cfg->rect_mode == GS_RECT_ELLIPSE)
-                emit_kernel<true><<<eblocks, 256, 0, s>>>(t, pdiv, (uint32_t)N, vin, sp.tiles, sp.rect, sp.rec,
-                                                          cfg->tile_w, cfg->tile_h, ek, ev, (uint32_t)capacity,
-                                                          hdr, U(L.st_emit), plan, thist);
-            else
-                emit_kernel<false><<<eblocks, 256, 0, s>>>(t, pdiv, (uint32_t)N, vin, sp.tiles, sp.rect, sp.rec,
-                                                           cfg->tile_w, cfg->tile_h, ek, ev, (uint32_t)capacity,
-                                                           hdr, U(L.st_emit), plan, thist);
-            count_launch();
-            GS_LAUNCH_CHECK();
-            // 4. tile sort
-            uint32_t *tki = ek, *tvi = ev, *tko = U(L.tk1), *tvo = (ev == d_vals) ? U(L.tv1) : d_vals;
-            for (int p = 0; p < plan.passes; ++p) {
-                cudaError_t e;
-                if (plan.bits[p] == 9)
-                    e = launch_onesweep<9>(L.parts_tile, s, tki, tvi, tko, tvo, &hdr->n_over,
-                                           plan.shift[p], thist + kHistSlot * p,
-                                           U(L.st_tile) + p * L.st_tile_stride,
-                                           &hdr->ctr[CTR_TILE + p], &hdr->err);
-                else
-                    e = launch_onesweep<8>(L.parts_tile, s, tki, tvi, tko, tvo, &hdr->n_over,
-                                           plan.shift[p], thist + kHistSlot * p,
-                                           U(L.st_tile) + p * L.st_tile_stride,
-                                           &hdr->ctr[CTR_TILE + p], &hdr->err);
-                if (e != cudaSuccess) {
-                    cudaGetLastError();
-                    return GS_ERR_CUDA;
-                }
-                std::swap(tki, tko);
-                std::swap(tvi, tvo);
+            uint2 *spans = U2(L.spans);
+            // 4. row split
+            // the opt-in is a cap on every later launch: set it once to the
+            // largest table any camera can need
+            const size_t sm_r = split_smem(bp.max_ty), sm_max = split_smem(kMaxDigits);
+            cudaError_t e = ell ? smem_optin(rows_kernel<true>, sm_max, optin_rows[1])
+                                : smem_optin(rows_kernel<false>, sm_max, optin_rows[0]);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return GS_ERR_CUDA;
             }
-            // 5. ranges (tki / tvi hold the sorted tile keys / record ids; tvi == d_vals)
-            const unsigned rblocks = (unsigned)std::min<int64_t>((capacity + 255) / 256, 148 * 16);
-            ranges_kernel<<<rblocks ? rblocks : 1, 256, 0, s>>>(
-                tki, tvi, sp.dkey, hdr, reinterpret_cast<uint2 *>(d_ranges),
-                reinterpret_cast<unsigned long long *>(d_keys64), (uint32_t)t.total_tiles, (uint32_t)N);
+            const unsigned gr = split_grid(L.max_rec_parts);
+            if (ell)
+                rows_kernel<true><<<gr, 256, sm_r, s>>>(bp, U(L.seg), U2(L.rec_parts), hdr, vin, sp.rect, sp.rec,
+                                                       (uint32_t)N, U(L.rowbase), spans, cap, U(L.st_rows), &hdr->ctr[CTR_ROWS],
+                                                       &hdr->err);
+            else
+                rows_kernel<false><<<gr, 256, sm_r, s>>>(bp, U(L.seg), U2(L.rec_parts), hdr, vin, sp.rect, sp.rec,
+                                                        (uint32_t)N, U(L.rowbase), spans, cap, U(L.st_rows), &hdr->ctr[CTR_ROWS],
+                                                        &hdr->err);
             count_launch();
             GS_LAUNCH_CHECK();
+            // 5. tile counts
+            const size_t sm_c = split_smem(bp.max_tx);
+            if (smem_optin(cols_count_kernel, sm_max, optin_cc) != cudaSuccess ||
+                smem_optin(cols_kernel, sm_max, optin_cols) != cudaSuccess) {
+                cudaGetLastError();
+                return GS_ERR_CUDA;
+            }
+            const unsigned gc = split_grid(L.max_span_parts);
+            cols_count_kernel<<<gc, 256, sm_c, s>>>(bp, U2(L.span_parts), hdr, U(L.rowbase), spans, cap,
+                                                    U(L.tile_cnt), &hdr->ctr[CTR_COUNT_COLS]);
+            count_launch();
+            GS_LAUNCH_CHECK();
+            // 6. tile ranges
+            tile_scan_kernel<<<(T + kScanTile - 1) / kScanTile, 256, 0, s>>>(U(L.tile_cnt), T, ranges, cap, hdr,
+                                                                            U(L.st_scan));
+            count_launch();
+            GS_LAUNCH_CHECK();
+            // 7. column split into the tiles' lists
+            cols_kernel<<<gc, 256, sm_c, s>>>(bp, U2(L.span_parts), hdr, U(L.rowbase), spans, cap, ranges, d_vals,
+                                              cap, U(L.st_cols), &hdr->ctr[CTR_COLS], &hdr->err);
+            count_launch();
+            GS_LAUNCH_CHECK();
+            if (d_keys64) {
+                const unsigned gk = (unsigned)std::min<int64_t>((T + 7) / 8, 148 * 16);
+                keys64_kernel<<<gk ? gk : 1, 256, 0, s>>>(ranges, T, d_vals, sp.dkey, (uint32_t)N,
+                                                         reinterpret_cast<unsigned long long *>(d_keys64));
+                count_launch();
+                GS_LAUNCH_CHECK();
+            }
+        } else {
+            if (cudaMemsetAsync(d_ranges, 0, sizeof(uint2) * (size_t)T, s) != cudaSuccess) return GS_ERR_CUDA;
         }
     }
     if (d_count) {
@@ -1023,7 +1378,7 @@ namespace gs {
 namespace {
 
 struct OrderWs {
-    size_t hdr, box, hist, st, k0, k1, v1, total;
+    size_t hdr, box, seg, hist, st, k0, k1, v1, total;
     uint32_t parts;
     size_t st_stride;
 };
@@ -1037,7 +1392,8 @@ OrderWs order_layout(int64_t P)
     L.st_stride = (size_t)256 * (L.parts + 1);
     L.hdr = take(sizeof(WsHeader));
     L.box = take(sizeof(uint32_t) * 6);
-    L.hist = take(sizeof(uint32_t) * 4 * kHistSlot);
+    L.seg = take(sizeof(uint32_t) * 2);
+    L.hist = take(sizeof(uint32_t) * 4 * 256);
     L.st = take(sizeof(uint32_t) * 4 * L.st_stride);
     L.k0 = take(sizeof(uint32_t) * P + 16);
     L.k1 = take(sizeof(uint32_t) * P + 16);
@@ -1058,11 +1414,14 @@ __device__ __forceinline__ float funord(uint32_t u)
 }
 
 // box[0..2] = images of the minima (start at all ones), box[3..5] = of the
-// maxima (start at zero); also publishes the element count for the sorts.
+// maxima (start at zero); also writes the sorts' one segment, [0, P).
 __global__ void __launch_bounds__(256) bbox_kernel(const float *__restrict__ means, int P, uint32_t *box,
-                                                   WsHeader *hdr)
+                                                   uint32_t *seg)
 {
-    if (blockIdx.x == 0 && threadIdx.x == 0) hdr->n_vis = (uint32_t)P;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        seg[0] = 0;
+        seg[1] = (uint32_t)P;
+    }
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
 #pragma unroll
@@ -1131,7 +1490,7 @@ __global__ void __launch_bounds__(256) morton_kernel(const float *__restrict__ m
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * 256; i += 256) {
         const uint32_t v = (&s_h[0][0])[i];
-        if (v) atomicAdd(&hist[(i >> 8) * kHistSlot + (i & 255)], v);
+        if (v) atomicAdd(&hist[i], v);
     }
 }
 
@@ -1174,7 +1533,7 @@ extern "C" gs_status gs_spatial_order(void *stream, int32_t P, const float *d_me
     if (cudaMemsetAsync(ws, 0, L.k0, s) != cudaSuccess) return GS_ERR_CUDA;
     if (cudaMemsetAsync(U(L.box), 0xff, sizeof(uint32_t) * 3, s) != cudaSuccess) return GS_ERR_CUDA;
     const unsigned blocks = (unsigned)std::min<int64_t>((P + 255) / 256, 148 * 8);
-    bbox_kernel<<<blocks, 256, 0, s>>>(d_means, P, U(L.box), hdr);
+    bbox_kernel<<<blocks, 256, 0, s>>>(d_means, P, U(L.box), U(L.seg));
     count_launch();
     GS_LAUNCH_CHECK();
     // (code, index) into (k0, d_perm); the passes ping-pong back into them
@@ -1183,8 +1542,9 @@ extern "C" gs_status gs_spatial_order(void *stream, int32_t P, const float *d_me
     GS_LAUNCH_CHECK();
     uint32_t *kin = U(L.k0), *vin = d_perm, *kout = U(L.k1), *vout = U(L.v1);
     for (int p = 0; p < 4; ++p) {
-        if (launch_onesweep<8>(L.parts, s, kin, vin, kout, vout, &hdr->n_vis, 8 * p, U(L.hist) + kHistSlot * p,
-                               U(L.st) + p * L.st_stride, &hdr->ctr[p], &hdr->err) != cudaSuccess) {
+        if (launch_onesweep<8>(L.parts, s, kin, vin, kout, vout, U(L.seg), nullptr, nullptr, 8 * p,
+                               U(L.hist) + 256 * p, 0, U(L.st) + p * L.st_stride, &hdr->ctr[p],
+                               &hdr->err) != cudaSuccess) {
             cudaGetLastError();
             return GS_ERR_CUDA;
         }

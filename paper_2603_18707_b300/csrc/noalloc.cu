@@ -57,9 +57,7 @@ extern "C" gs_status gs_bin_sort_noalloc(void *stream, const gs_camera *cams, in
                                          uint64_t *d_keys64, uint32_t *d_count, uint32_t *d_error)
 {
     if (!cams || !cfg || ncam <= 0 || ncam > GS_MAX_CAMERAS || P < 0 || capacity < 0) return GS_ERR_ARG;
-    const int64_t tiles = gs_total_tiles(cams, ncam, cfg);
-    if (tiles < 0) return GS_ERR_ARG;
-    const size_t need = gs_bin_sort_workspace_bytes((int64_t)ncam * P, capacity, tiles);
+    const size_t need = gs_bin_sort_workspace_bytes(cams, ncam, P, cfg, capacity);
     if (need == 0 || need > kNoAllocBytes) return GS_ERR_ARG; // beyond the static scratch
     void *ws = nullptr;
     const gs_status st = scratch_for_current_device(&ws);

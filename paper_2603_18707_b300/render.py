@@ -98,8 +98,7 @@ class Rasterizer:
 
     def _alloc(self, capacity: int):
         self.capacity = int(capacity)
-        n_rec = self.ncam * self.P
-        ws = api.gs_bin_sort_workspace_bytes(n_rec, self.capacity, self.total_tiles)
+        ws = api.gs_bin_sort_workspace_bytes(self.cams, self.P, self.cfg, self.capacity)
         self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
         self.vals = torch.empty(max(self.capacity, 1), dtype=torch.int32, device=self.device)
         self.keys64 = (torch.empty(max(self.capacity, 1), dtype=torch.int64, device=self.device)

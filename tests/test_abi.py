@@ -76,7 +76,9 @@ def test_sizes_and_tiles(L):
     cfg8 = api.make_config("poly1", "opacity", tile=(8, 8))
     assert api.gs_total_tiles(cams, cfg8) == 256 + 13 * 10
     assert api.gs_splat2d_bytes(2, 1000) >= 2 * 1000 * 64
-    assert api.gs_bin_sort_workspace_bytes(1000, 5000, 99) > 4 * 5000 * 3
+    assert api.gs_bin_sort_workspace_bytes(cams, 500, cfg, 5000) > 8 * 5000 + 16 * 1000
+    assert api.gs_bin_sort_workspace_bytes(cams, -1, cfg, 5000) == 0
+    assert api.gs_bin_sort_workspace_bytes(cams, 500, cfg, -1) == 0
 
 
 def test_host_argument_checks(L):

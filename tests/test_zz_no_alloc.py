@@ -52,7 +52,7 @@ def test_noalloc_matches_workspace_path_twice(gs):
         torch.cuda.synchronize()
         n_over = R.n_records()[1]
         capacity = n_over + 1000
-        assert api.gs_bin_sort_workspace_bytes(R.ncam * R.P, capacity, R.total_tiles) <= 32 << 20
+        assert api.gs_bin_sort_workspace_bytes(R.cams, R.P, cfg, capacity) <= 32 << 20
         vals, ranges, keys, count, err, grew = _noalloc(api, R, capacity)
         assert err == 0
         assert grew == 0, f"free device memory fell by {grew} bytes during the call"
