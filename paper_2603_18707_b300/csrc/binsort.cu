@@ -59,8 +59,9 @@ constexpr int kSpinLimit = 1 << 20;
 #define GS_LOOK_WINDOW 1
 #endif
 #ifndef GS_SPLIT_BLOCKS
-#define GS_SPLIT_BLOCKS 4 // resident CTAs per SM of the persistent split kernels
+#define GS_SPLIT_BLOCKS 3 // register budget of the split kernels: CTAs per SM it allows
 #endif
+#define GS_SPLIT_BOUNDS __launch_bounds__(256, GS_SPLIT_BLOCKS)
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = GS_SORT_ITEMS;
 constexpr int kSortTile = kSortThreads * kSortItems; // keys per partition
@@ -78,6 +79,14 @@ constexpr int kScanItems = 16;
 constexpr int kScanTile = 256 * kScanItems;          // tiles per scan partition
 constexpr int kMaxDigits = 2048;                     // tile rows / columns per camera (16384 px / 8)
 constexpr int kLookWindow = GS_LOOK_WINDOW;
+#ifndef GS_SPLIT_WINDOW
+#define GS_SPLIT_WINDOW 16
+#endif
+// Look-back window of the split kernels: their partitions start together in
+// long segments (a camera has hundreds of row-split partitions), so a
+// partition may have to walk back over many predecessors that have only
+// published their counts; several loads per round shorten the walk.
+constexpr int kSplitWindow = GS_SPLIT_WINDOW;
 
 enum Counter {
     CTR_COMPACT = 0,
@@ -220,6 +229,29 @@ __device__ __forceinline__ uint32_t warp_peers(uint32_t d)
 #endif
 }
 
+#ifndef GS_SPLIT_RANK
+#define GS_SPLIT_RANK 1
+#endif
+// Place of this lane's item among the warp's items with the same digit d
+// (d < 2048), in lane order, after the warp's running count of d in wc[d];
+// advances wc[d] by the group's size. Inactive lanes take no place. Peers by
+// ballots over the digit bits (GS_SPLIT_RANK 1) or the match instruction (0).
+__device__ __forceinline__ uint32_t split_rank(uint32_t *wc, uint32_t d, bool act, uint32_t lt)
+{
+    const int lane = threadIdx.x & 31;
+#if GS_SPLIT_RANK
+    const uint32_t peers = warp_peers<11>(d) & __ballot_sync(0xffffffffu, act);
+#else
+    const uint32_t peers = __match_any_sync(0xffffffffu, act ? d : 0x10000u + lane) & __ballot_sync(0xffffffffu, act);
+#endif
+    // every lane of a group reads the count before its first lane moves it on
+    const uint32_t base = act ? wc[d] : 0u;
+    __syncwarp();
+    if (act && lane == __ffs(peers) - 1) wc[d] = base + __popc(peers);
+    __syncwarp();
+    return base + __popc(peers & lt);
+}
+
 __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b)
 {
     uint32_t s = a + b;
@@ -272,6 +304,7 @@ __device__ uint32_t lookback_scalar(uint32_t *state, uint32_t part, uint32_t agg
 // walk never leaves the segment. A predecessor that has published nothing is
 // re-read after a short sleep, at most `limit` times; then GS_ERR_TIMEOUT is
 // raised and what was summed is returned.
+template <int WIN = kLookWindow>
 __device__ uint32_t lookback_digit(const uint32_t *state, uint32_t part, int R, int d, uint32_t *err,
                                    int limit)
 {
@@ -280,14 +313,14 @@ __device__ uint32_t lookback_digit(const uint32_t *state, uint32_t part, int R, 
     int spins = 0;
     bool done = false;
     while (!done && p >= 0) {
-        uint32_t s[kLookWindow];
+        uint32_t s[WIN];
 #pragma unroll
-        for (int w = 0; w < kLookWindow; ++w)
+        for (int w = 0; w < WIN; ++w)
             s[w] = (p - w >= 0) ? ld_relaxed(&state[(size_t)(p - w) * R + d]) : kFlagIncl;
         int used = 0;
         bool stall = false;
 #pragma unroll
-        for (int w = 0; w < kLookWindow; ++w) {
+        for (int w = 0; w < WIN; ++w) {
             if (done || stall) continue;
             const uint32_t f = s[w] >> 30;
             if (f == 0) {
@@ -312,7 +345,8 @@ __device__ uint32_t lookback_digit(const uint32_t *state, uint32_t part, int R, 
 
 // Publishes digit d's count of partition `part` (chunk > 0: of a segment
 // that began in an earlier partition) and returns the digit's exclusive
-// prefix within the segment.
+// prefix within the segment; WIN predecessors per load round.
+template <int WIN>
 __device__ __forceinline__ uint32_t publish_digit(uint32_t *state, uint32_t part, uint32_t chunk, int R, int d,
                                                   uint32_t agg, uint32_t *err)
 {
@@ -322,7 +356,7 @@ __device__ __forceinline__ uint32_t publish_digit(uint32_t *state, uint32_t part
         return 0;
     }
     st_relaxed(st, kFlagAgg | agg);
-    const uint32_t excl = lookback_digit(state, part, R, d, err, kSpinLimit);
+    const uint32_t excl = lookback_digit<WIN>(state, part, R, d, err, kSpinLimit);
     st_relaxed(st, kFlagIncl | sat_add(excl, agg));
     return excl;
 }
@@ -672,7 +706,7 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
         s_bexcl[d] = bex;
         bex += cnt[q];
         const uint32_t agg = cnt[q] - (d == (int)M ? n_invalid : 0u);
-        const uint32_t excl = publish_digit(state, part, chunk, R, d, agg, err);
+        const uint32_t excl = publish_digit<kLookWindow>(state, part, chunk, R, d, agg, err);
         s_goff[d] = hex + excl;
         hex += hv[q];
     }
@@ -710,7 +744,7 @@ inline size_t split_smem(int max_digits) { return sizeof(uint32_t) * (8 * (size_
 // this warp. Span = (record index, first column | last column << 16); a row
 // the ellipse misses (GS_RECT_ELLIPSE) gets an empty span (first > last).
 template <bool ELL>
-__global__ void __launch_bounds__(256)
+__global__ void GS_SPLIT_BOUNDS
 rows_kernel(const __grid_constant__ BinPlan bp, const uint32_t *__restrict__ seg, const uint2 *__restrict__ parts,
             const WsHeader *hdr, const uint32_t *__restrict__ ids, const ushort4 *__restrict__ rects,
             const float4 *__restrict__ rec, uint32_t N, const uint32_t *__restrict__ rowbase,
@@ -741,17 +775,29 @@ rows_kernel(const __grid_constant__ BinPlan bp, const uint32_t *__restrict__ seg
         auto usable = [&](uint32_t id, ushort4 r) {
             return id < N && r.y <= r.w && r.w < ty && r.x <= r.z && r.z < tx;
         };
-        // per-warp row counts as a difference array
-#pragma unroll 4
+        // this thread's records, all loads in flight at once: index, then
+        // rectangle as first | last column and first | last row (rows
+        // 0xffff | 0 marks a record to skip)
+        uint32_t rid[kRowItems], rxr[kRowItems], ryr[kRowItems];
+#pragma unroll
         for (int j = 0; j < kRowItems; ++j) {
             const uint32_t idx = wb + 32 * j + lane;
-            if (idx < end) {
-                const uint32_t id = ids[idx];
-                const ushort4 r = id < N ? rects[id] : make_ushort4(1, 1, 0, 0);
-                if (usable(id, r)) {
-                    atomicAdd(&wc[r.y], 1u);
-                    atomicAdd(&wc[r.w + 1], 0xffffffffu);
-                }
+            rid[j] = idx < end ? ids[idx] : N;
+        }
+#pragma unroll
+        for (int j = 0; j < kRowItems; ++j) {
+            const ushort4 r = rid[j] < N ? rects[rid[j]] : make_ushort4(1, 1, 0, 0);
+            const bool ok = usable(rid[j], r);
+            rxr[j] = (uint32_t)r.x | ((uint32_t)r.z << 16);
+            ryr[j] = ok ? ((uint32_t)r.y | ((uint32_t)r.w << 16)) : 0xffffu;
+        }
+        // per-warp row counts as a difference array
+#pragma unroll
+        for (int j = 0; j < kRowItems; ++j) {
+            const uint32_t y0 = ryr[j] & 0xffffu, y1 = ryr[j] >> 16;
+            if (y0 <= y1) {
+                atomicAdd(&wc[y0], 1u);
+                atomicAdd(&wc[y1 + 1], 0xffffffffu);
             }
         }
         __syncwarp();
@@ -772,29 +818,20 @@ rows_kernel(const __grid_constant__ BinPlan bp, const uint32_t *__restrict__ seg
                 s_cnt[w * D + y] = a;
                 a += x;
             }
-            const uint32_t base = rowbase[gp + y] + publish_digit(state, part, chunk, bp.max_ty, y, a, err);
+            const uint32_t base = rowbase[gp + y] + publish_digit<kSplitWindow>(state, part, chunk, bp.max_ty, y, a, err);
 #pragma unroll
             for (int w = 0; w < 8; ++w) s_cnt[w * D + y] += base;
         }
         __syncthreads();
         const int W = bp.cam[c].W, H = bp.cam[c].H;
+#pragma unroll
         for (int j = 0; j < kRowItems; ++j) {
             if (wb + 32 * j >= end) break; // uniform per warp
-            const uint32_t idx = wb + 32 * j + lane;
-            uint32_t id = 0, h = 0;
-            ushort4 r = make_ushort4(0, 0, 0, 0);
-            if (idx < end) {
-                id = ids[idx];
-                r = id < N ? rects[id] : make_ushort4(1, 1, 0, 0);
-                if (usable(id, r))
-                    h = (uint32_t)r.w - r.y + 1u;
-                else
-                    r = make_ushort4(0, 0, 0, 0);
-            }
+            const uint32_t id = rid[j], xr = rxr[j], yr = ryr[j];
+            const uint32_t y0 = yr & 0xffffu, y1 = yr >> 16;
+            const uint32_t h = y0 <= y1 ? y1 - y0 + 1u : 0u;
             const uint32_t incl = warp_incl_scan(h);
             const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
-            const uint32_t xr = (uint32_t)r.x | ((uint32_t)r.z << 16);
-            const uint32_t yr = (uint32_t)r.y | ((uint32_t)r.w << 16);
             for (uint32_t b = 0; b < tot; b += 32) {
                 const uint32_t p = b + lane;
                 const uint32_t pq = min(p, tot - 1u);
@@ -818,17 +855,8 @@ rows_kernel(const __grid_constant__ BinPlan bp, const uint32_t *__restrict__ seg
                                      : 0xffffu;
                     }
                 }
-                const uint32_t peers = __match_any_sync(0xffffffffu, act ? y : 0x10000u + lane);
-                const int leader = __ffs(peers) - 1;
-                uint32_t base = 0;
-                if (act && lane == leader) {
-                    base = wc[y];
-                    wc[y] = base + __popc(peers);
-                }
-                base = __shfl_sync(0xffffffffu, base, leader);
-                const uint32_t pos = base + __popc(peers & lt);
+                const uint32_t pos = split_rank(wc, act ? y : 0u, act, lt);
                 if (act && pos < span_cap) spans[pos] = make_uint2(eid, span_x);
-                __syncwarp();
             }
         }
         __syncthreads();
@@ -857,7 +885,7 @@ __device__ __forceinline__ SpanPart span_part(const BinPlan &bp, const uint2 *pa
 
 // 5. tile counts: per span partition a difference array over the row's
 // columns, added to the tiles' counters.
-__global__ void __launch_bounds__(256)
+__global__ void GS_SPLIT_BOUNDS
 cols_count_kernel(const __grid_constant__ BinPlan bp, const uint2 *__restrict__ parts, const WsHeader *hdr,
                   const uint32_t *__restrict__ rowbase, const uint2 *__restrict__ spans, uint32_t span_cap,
                   uint32_t *__restrict__ tile_cnt, uint32_t *ctr)
@@ -940,7 +968,7 @@ tile_scan_kernel(const uint32_t *__restrict__ tile_cnt, uint32_t T, uint2 *__res
 // partitions (look-back) + in earlier warps + earlier in this warp. Writes
 // the record index there (places at or past the capacity are dropped; the
 // overflow is flagged by the plan).
-__global__ void __launch_bounds__(256)
+__global__ void GS_SPLIT_BOUNDS
 cols_kernel(const __grid_constant__ BinPlan bp, const uint2 *__restrict__ parts, const WsHeader *hdr,
             const uint32_t *__restrict__ rowbase, const uint2 *__restrict__ spans, uint32_t span_cap,
             const uint2 *__restrict__ ranges, uint32_t *__restrict__ vals, uint32_t cap, uint32_t *state,
@@ -964,16 +992,23 @@ cols_kernel(const __grid_constant__ BinPlan bp, const uint2 *__restrict__ parts,
         const int tx = bp.cam[sp.c].tiles_x;
         if (sp.y >= bp.cam[sp.c].tiles_y) sp.end = sp.beg; // the padding row has no spans
         const uint32_t wb = sp.beg + warp * (32 * kColItems);
-#pragma unroll 4
+        // this thread's spans, all loads in flight at once (columns 0xffff | 0
+        // mark an empty span or a slot past the partition)
+        uint32_t sid[kColItems], sxr[kColItems];
+#pragma unroll
         for (int j = 0; j < kColItems; ++j) {
             const uint32_t idx = wb + 32 * j + lane;
-            if (idx < sp.end) {
-                const uint32_t xr = spans[idx].y;
-                const uint32_t x0 = xr & 0xffffu, x1 = xr >> 16;
-                if (x0 <= x1 && x1 < (uint32_t)tx) {
-                    atomicAdd(&wc[x0], 1u);
-                    atomicAdd(&wc[x1 + 1], 0xffffffffu);
-                }
+            const uint2 v = idx < sp.end ? spans[idx] : make_uint2(0u, 0xffffu);
+            const uint32_t x0 = v.y & 0xffffu, x1 = v.y >> 16;
+            sid[j] = v.x;
+            sxr[j] = (x0 <= x1 && x1 < (uint32_t)tx) ? v.y : 0xffffu;
+        }
+#pragma unroll
+        for (int j = 0; j < kColItems; ++j) {
+            const uint32_t x0 = sxr[j] & 0xffffu, x1 = sxr[j] >> 16;
+            if (x0 <= x1) {
+                atomicAdd(&wc[x0], 1u);
+                atomicAdd(&wc[x1 + 1], 0xffffffffu);
             }
         }
         __syncwarp();
@@ -994,22 +1029,16 @@ cols_kernel(const __grid_constant__ BinPlan bp, const uint2 *__restrict__ parts,
                 s_cnt[w * D + x] = a;
                 a += v;
             }
-            const uint32_t base = ranges[trow + x].x + publish_digit(state, part, sp.chunk, bp.max_tx, x, a, err);
+            const uint32_t base = ranges[trow + x].x + publish_digit<kSplitWindow>(state, part, sp.chunk, bp.max_tx, x, a, err);
 #pragma unroll
             for (int w = 0; w < 8; ++w) s_cnt[w * D + x] += base;
         }
         __syncthreads();
+#pragma unroll
         for (int j = 0; j < kColItems; ++j) {
             if (wb + 32 * j >= sp.end) break; // uniform per warp
-            const uint32_t idx = wb + 32 * j + lane;
-            uint32_t id = 0, n = 0, x0 = 0;
-            if (idx < sp.end) {
-                const uint2 s = spans[idx];
-                id = s.x;
-                x0 = s.y & 0xffffu;
-                const uint32_t x1 = s.y >> 16;
-                n = (x0 <= x1 && x1 < (uint32_t)tx) ? x1 - x0 + 1u : 0u;
-            }
+            const uint32_t id = sid[j], x0 = sxr[j] & 0xffffu, x1 = sxr[j] >> 16;
+            const uint32_t n = x0 <= x1 ? x1 - x0 + 1u : 0u;
             const uint32_t incl = warp_incl_scan(n);
             const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
             for (uint32_t b = 0; b < tot; b += 32) {
@@ -1021,17 +1050,205 @@ cols_kernel(const __grid_constant__ BinPlan bp, const uint2 *__restrict__ parts,
                 const uint32_t ebeg = __shfl_sync(0xffffffffu, incl - n, e);
                 const bool act = p < tot;
                 const uint32_t x = ex0 + (pq - ebeg);
-                const uint32_t peers = __match_any_sync(0xffffffffu, act ? x : 0x10000u + lane);
-                const int leader = __ffs(peers) - 1;
-                uint32_t base = 0;
-                if (act && lane == leader) {
-                    base = wc[x];
-                    wc[x] = base + __popc(peers);
-                }
-                base = __shfl_sync(0xffffffffu, base, leader);
-                const uint32_t pos = base + __popc(peers & lt);
+                const uint32_t pos = split_rank(wc, act ? x : 0u, act, lt);
                 if (act && pos < cap) vals[pos] = eid;
-                __syncwarp();
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---- split kernels with thread-private counters ---------------------------
+// The same two splits for cameras of at most kThreadDigits tile rows /
+// columns. Thread t of a partition owns its items [beg + I t, beg + I (t + 1)),
+// I = 20, in order, and a private 16-bit counter per digit in shared memory
+// (cnt[d][t]). Stable places then need no ranking inside a warp: count each
+// thread's items per digit, turn the counters into the exclusive prefix over
+// the threads (plus the digit's offset from the look-back), and let every
+// thread write its items in order, taking and advancing its own counter.
+// Counts per thread are at most I x (digits covered), prefixes at most the
+// partition's items (kSortTile or kColTile records / spans): 16 bits hold both
+// as long as a digit's prefix stays below 2^16, i.e. any partition here.
+constexpr int kThreadDigits = 384;
+constexpr int kTItems = 20;
+static_assert(kTItems * 256 == kSortTile && kTItems * 256 == kColTile, "partition sizes");
+
+inline size_t tsplit_smem(int max_digits)
+{
+    return sizeof(uint16_t) * 256 * (size_t)max_digits + sizeof(uint32_t) * ((size_t)max_digits + 4);
+}
+
+// cnt[d][0..256) for d < nd: exclusive prefix over the threads in place; the
+// digit's total to tot[d]. Warp w takes digits w, w + 8, ...; lane l holds
+// threads 8 l .. 8 l + 7 (one 16-byte word).
+__device__ __forceinline__ void tsplit_scan(uint16_t *cnt, uint32_t *tot, int nd)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = warp; d < nd; d += 8) {
+        uint4 *row = reinterpret_cast<uint4 *>(cnt + (size_t)d * 256);
+        const uint4 q = row[lane];
+        uint32_t w[4] = {q.x, q.y, q.z, q.w};
+        uint32_t s = 0, v[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[2 * k] = w[k] & 0xffffu;
+            v[2 * k + 1] = w[k] >> 16;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t x = v[k];
+            v[k] = s;
+            s += x;
+        }
+        const uint32_t incl = warp_incl_scan(s);
+        const uint32_t ex = incl - s;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w[k] = ((v[2 * k] + ex) & 0xffffu) | ((v[2 * k + 1] + ex) << 16);
+        row[lane] = make_uint4(w[0], w[1], w[2], w[3]);
+        if (lane == 31) tot[d] = incl;
+    }
+}
+
+template <bool ELL>
+__global__ void __launch_bounds__(256, 2)
+rows_t_kernel(const __grid_constant__ BinPlan bp, const uint32_t *__restrict__ seg, const uint2 *__restrict__ parts,
+              const WsHeader *hdr, const uint32_t *__restrict__ ids, const ushort4 *__restrict__ rects,
+              const float4 *__restrict__ rec, uint32_t N, const uint32_t *__restrict__ rowbase,
+              uint2 *__restrict__ spans, uint32_t span_cap, uint32_t *state, uint32_t *ctr, uint32_t *err)
+{
+    extern __shared__ uint32_t smem[];
+    const int ND = bp.max_ty;
+    uint16_t *cnt = reinterpret_cast<uint16_t *>(smem); // [ND][256]
+    uint32_t *sbase = smem + (size_t)ND * 128;           // [ND]
+    uint32_t *s_part = sbase + ND;
+    const int tid = threadIdx.x;
+    const uint32_t nparts = hdr->n_rec_parts;
+    while (true) {
+        {
+            uint4 *z = reinterpret_cast<uint4 *>(smem);
+            for (int i = tid; i < ND * 32; i += 256) z[i] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        if (tid == 0) *s_part = atomicAdd(ctr, 1u);
+        __syncthreads();
+        const uint32_t part = *s_part;
+        if (part >= nparts) break;
+        const uint2 pc = parts[part];
+        const int c = (int)pc.x;
+        const uint32_t chunk = pc.y;
+        const uint32_t beg = seg[c] + chunk * kRowTile, end = min(seg[c + 1], beg + kRowTile);
+        const int ty = bp.cam[c].tiles_y, tx = bp.cam[c].tiles_x;
+        const uint32_t t0 = beg + tid * kTItems;
+        uint32_t rid[kTItems], rxr[kTItems], ryr[kTItems];
+#pragma unroll
+        for (int j = 0; j < kTItems; ++j) rid[j] = t0 + j < end ? ids[t0 + j] : N;
+#pragma unroll
+        for (int j = 0; j < kTItems; ++j) {
+            const ushort4 r = rid[j] < N ? rects[rid[j]] : make_ushort4(1, 1, 0, 0);
+            // a drawn record's rectangle lies inside its camera's grid; the
+            // check only matters after a timed-out wait left stale entries
+            const bool ok = rid[j] < N && r.y <= r.w && r.w < ty && r.x <= r.z && r.z < tx;
+            rxr[j] = (uint32_t)r.x | ((uint32_t)r.z << 16);
+            ryr[j] = ok ? ((uint32_t)r.y | ((uint32_t)r.w << 16)) : 0xffffu;
+        }
+        uint16_t *my = cnt + tid;
+#pragma unroll
+        for (int j = 0; j < kTItems; ++j) {
+            const int y1 = (int)(ryr[j] >> 16);
+            for (int y = (int)(ryr[j] & 0xffffu); y <= y1; ++y) my[y * 256] += 1;
+        }
+        __syncthreads();
+        tsplit_scan(cnt, sbase, ty);
+        __syncthreads();
+        const int gp = bp.cam[c].gpad;
+        for (int y = tid; y < ty; y += 256)
+            sbase[y] = rowbase[gp + y] + publish_digit<kSplitWindow>(state, part, chunk, bp.max_ty, y, sbase[y], err);
+        __syncthreads();
+        const int W = bp.cam[c].W, H = bp.cam[c].H;
+#pragma unroll
+        for (int j = 0; j < kTItems; ++j) {
+            const int y0 = (int)(ryr[j] & 0xffffu), y1 = (int)(ryr[j] >> 16);
+            const uint32_t id = rid[j];
+            const int x0 = (int)(rxr[j] & 0xffffu), x1 = (int)(rxr[j] >> 16);
+            float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
+            const bool cut = ELL && y0 < y1 && x0 < x1; // a single row or column keeps its tiles
+            if (cut) {
+                g0 = rec[3 * (size_t)id];
+                g1 = rec[3 * (size_t)id + 1];
+            }
+            for (int y = y0; y <= y1; ++y) {
+                const uint32_t k = my[y * 256];
+                my[y * 256] = (uint16_t)(k + 1u);
+                const uint32_t pos = sbase[y] + k;
+                uint32_t sx = rxr[j];
+                if (cut) {
+                    int a0, a1;
+                    sx = row_cols(g0.x, g0.y, g1.x, g1.y, g1.z, g1.w, y, bp.tile_w, bp.tile_h, W, H, x0, x1, a0, a1)
+                             ? ((uint32_t)a0 | ((uint32_t)a1 << 16))
+                             : 0xffffu;
+                }
+                if (pos < span_cap) spans[pos] = make_uint2(id, sx);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void GS_SPLIT_BOUNDS
+cols_t_kernel(const __grid_constant__ BinPlan bp, const uint2 *__restrict__ parts, const WsHeader *hdr,
+              const uint32_t *__restrict__ rowbase, const uint2 *__restrict__ spans, uint32_t span_cap,
+              const uint2 *__restrict__ ranges, uint32_t *__restrict__ vals, uint32_t cap, uint32_t *state,
+              uint32_t *ctr, uint32_t *err)
+{
+    extern __shared__ uint32_t smem[];
+    const int ND = bp.max_tx;
+    uint16_t *cnt = reinterpret_cast<uint16_t *>(smem); // [ND][256]
+    uint32_t *sbase = smem + (size_t)ND * 128;           // [ND]
+    uint32_t *s_part = sbase + ND;
+    const int tid = threadIdx.x;
+    const uint32_t nparts = hdr->n_span_parts;
+    while (true) {
+        {
+            uint4 *z = reinterpret_cast<uint4 *>(smem);
+            for (int i = tid; i < ND * 32; i += 256) z[i] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        if (tid == 0) *s_part = atomicAdd(ctr, 1u);
+        __syncthreads();
+        const uint32_t part = *s_part;
+        if (part >= nparts) break;
+        SpanPart sp = span_part(bp, parts, part, rowbase, span_cap);
+        const int tx = bp.cam[sp.c].tiles_x;
+        if (sp.y >= bp.cam[sp.c].tiles_y) sp.end = sp.beg; // the padding row has no spans
+        const uint32_t t0 = sp.beg + tid * kTItems;
+        uint32_t sid[kTItems], sxr[kTItems];
+#pragma unroll
+        for (int j = 0; j < kTItems; ++j) {
+            const uint2 v = t0 + j < sp.end ? spans[t0 + j] : make_uint2(0u, 0xffffu);
+            const uint32_t x0 = v.y & 0xffffu, x1 = v.y >> 16;
+            sid[j] = v.x;
+            sxr[j] = (x0 <= x1 && x1 < (uint32_t)tx) ? v.y : 0xffffu;
+        }
+        uint16_t *my = cnt + tid;
+#pragma unroll
+        for (int j = 0; j < kTItems; ++j) {
+            const int x1 = (int)(sxr[j] >> 16);
+            for (int x = (int)(sxr[j] & 0xffffu); x <= x1; ++x) my[x * 256] += 1;
+        }
+        __syncthreads();
+        tsplit_scan(cnt, sbase, tx);
+        __syncthreads();
+        const uint32_t trow = (uint32_t)bp.cam[sp.c].tile_base + (uint32_t)sp.y * tx;
+        for (int x = tid; x < tx; x += 256)
+            sbase[x] = ranges[trow + x].x + publish_digit<kSplitWindow>(state, part, sp.chunk, bp.max_tx, x, sbase[x], err);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kTItems; ++j) {
+            const int x1 = (int)(sxr[j] >> 16);
+            const uint32_t id = sid[j];
+            for (int x = (int)(sxr[j] & 0xffffu); x <= x1; ++x) {
+                const uint32_t k = my[x * 256];
+                my[x * 256] = (uint16_t)(k + 1u);
+                const uint32_t pos = sbase[x] + k;
+                if (pos < cap) vals[pos] = id;
             }
         }
         __syncthreads();
@@ -1149,9 +1366,11 @@ cudaError_t launch_onesweep(unsigned grid, cudaStream_t s, const uint32_t *ki, c
     return cudaPeekAtLastError();
 }
 
-// Grid of a persistent split kernel: every SM filled, never more CTAs than
-// partitions can exist.
-unsigned split_grid(uint32_t max_parts)
+// Grid of a persistent split kernel: as many CTAs as fit on every SM at once
+// (so that no partition waits for a CTA that is not resident), never more
+// than partitions can exist.
+template <typename K>
+unsigned split_grid(K kernel, size_t smem, uint32_t max_parts)
 {
     static int sms[64] = {};
     int dev = 0;
@@ -1161,7 +1380,12 @@ unsigned split_grid(uint32_t max_parts)
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
         if (dev < 64) sms[dev] = n;
     }
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)n * GS_SPLIT_BLOCKS, max_parts));
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem) != cudaSuccess || per_sm <= 0) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)n * per_sm, max_parts));
 }
 
 } // namespace
@@ -1210,7 +1434,8 @@ extern "C" gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t nc
     if (N == 0) {
         if (cudaMemsetAsync(d_ranges, 0, sizeof(uint2) * (size_t)T, s) != cudaSuccess) return GS_ERR_CUDA;
     } else {
-        static bool optin_rows[2][64] = {}, optin_cc[64] = {}, optin_cols[64] = {};
+        static bool optin_rows[2][64] = {}, optin_rows_t[2][64] = {}, optin_cc[64] = {}, optin_cols[64] = {},
+                    optin_cols_t[64] = {};
         Splat2DConst sp = splat2d_const(d_splat2d, N);
         const bool ell = cfg->rect_mode == GS_RECT_ELLIPSE;
         // 1. compaction, per-camera histograms and row differences
@@ -1239,37 +1464,56 @@ extern "C" gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t nc
         }
         if (capacity > 0) {
             uint2 *spans = U2(L.spans);
+            // the dynamic shared-memory opt-ins are caps on every later launch:
+            // each is set once, to the largest table any camera can need
+            const size_t smw_max = split_smem(kMaxDigits), smt_max = tsplit_smem(kThreadDigits);
+            const bool rows_t = bp.max_ty <= kThreadDigits, cols_t = bp.max_tx <= kThreadDigits;
+            cudaError_t e = cudaSuccess;
             // 4. row split
-            // the opt-in is a cap on every later launch: set it once to the
-            // largest table any camera can need
-            const size_t sm_r = split_smem(bp.max_ty), sm_max = split_smem(kMaxDigits);
-            cudaError_t e = ell ? smem_optin(rows_kernel<true>, sm_max, optin_rows[1])
-                                : smem_optin(rows_kernel<false>, sm_max, optin_rows[0]);
+            const size_t sm_r = rows_t ? tsplit_smem(bp.max_ty) : split_smem(bp.max_ty);
+            unsigned gr = 0;
+            if (rows_t && ell) {
+                e = smem_optin(rows_t_kernel<true>, smt_max, optin_rows_t[1]);
+                gr = split_grid(rows_t_kernel<true>, sm_r, L.max_rec_parts);
+            } else if (rows_t) {
+                e = smem_optin(rows_t_kernel<false>, smt_max, optin_rows_t[0]);
+                gr = split_grid(rows_t_kernel<false>, sm_r, L.max_rec_parts);
+            } else if (ell) {
+                e = smem_optin(rows_kernel<true>, smw_max, optin_rows[1]);
+                gr = split_grid(rows_kernel<true>, sm_r, L.max_rec_parts);
+            } else {
+                e = smem_optin(rows_kernel<false>, smw_max, optin_rows[0]);
+                gr = split_grid(rows_kernel<false>, sm_r, L.max_rec_parts);
+            }
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 return GS_ERR_CUDA;
             }
-            const unsigned gr = split_grid(L.max_rec_parts);
-            if (ell)
-                rows_kernel<true><<<gr, 256, sm_r, s>>>(bp, U(L.seg), U2(L.rec_parts), hdr, vin, sp.rect, sp.rec,
-                                                       (uint32_t)N, U(L.rowbase), spans, cap, U(L.st_rows), &hdr->ctr[CTR_ROWS],
-                                                       &hdr->err);
+#define GS_ROWS_ARGS                                                                                           \
+    bp, U(L.seg), U2(L.rec_parts), hdr, vin, sp.rect, sp.rec, (uint32_t)N, U(L.rowbase), spans, cap, U(L.st_rows), \
+        &hdr->ctr[CTR_ROWS], &hdr->err
+            if (rows_t && ell)
+                rows_t_kernel<true><<<gr, 256, sm_r, s>>>(GS_ROWS_ARGS);
+            else if (rows_t)
+                rows_t_kernel<false><<<gr, 256, sm_r, s>>>(GS_ROWS_ARGS);
+            else if (ell)
+                rows_kernel<true><<<gr, 256, sm_r, s>>>(GS_ROWS_ARGS);
             else
-                rows_kernel<false><<<gr, 256, sm_r, s>>>(bp, U(L.seg), U2(L.rec_parts), hdr, vin, sp.rect, sp.rec,
-                                                        (uint32_t)N, U(L.rowbase), spans, cap, U(L.st_rows), &hdr->ctr[CTR_ROWS],
-                                                        &hdr->err);
+                rows_kernel<false><<<gr, 256, sm_r, s>>>(GS_ROWS_ARGS);
+#undef GS_ROWS_ARGS
             count_launch();
             GS_LAUNCH_CHECK();
             // 5. tile counts
-            const size_t sm_c = split_smem(bp.max_tx);
-            if (smem_optin(cols_count_kernel, sm_max, optin_cc) != cudaSuccess ||
-                smem_optin(cols_kernel, sm_max, optin_cols) != cudaSuccess) {
+            const size_t sm_cc = split_smem(bp.max_tx);
+            const size_t sm_c = cols_t ? tsplit_smem(bp.max_tx) : sm_cc;
+            if (smem_optin(cols_count_kernel, smw_max, optin_cc) != cudaSuccess ||
+                (cols_t ? smem_optin(cols_t_kernel, smt_max, optin_cols_t)
+                        : smem_optin(cols_kernel, smw_max, optin_cols)) != cudaSuccess) {
                 cudaGetLastError();
                 return GS_ERR_CUDA;
             }
-            const unsigned gc = split_grid(L.max_span_parts);
-            cols_count_kernel<<<gc, 256, sm_c, s>>>(bp, U2(L.span_parts), hdr, U(L.rowbase), spans, cap,
-                                                    U(L.tile_cnt), &hdr->ctr[CTR_COUNT_COLS]);
+            cols_count_kernel<<<split_grid(cols_count_kernel, sm_cc, L.max_span_parts), 256, sm_cc, s>>>(
+                bp, U2(L.span_parts), hdr, U(L.rowbase), spans, cap, U(L.tile_cnt), &hdr->ctr[CTR_COUNT_COLS]);
             count_launch();
             GS_LAUNCH_CHECK();
             // 6. tile ranges
@@ -1278,8 +1522,14 @@ extern "C" gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t nc
             count_launch();
             GS_LAUNCH_CHECK();
             // 7. column split into the tiles' lists
-            cols_kernel<<<gc, 256, sm_c, s>>>(bp, U2(L.span_parts), hdr, U(L.rowbase), spans, cap, ranges, d_vals,
-                                              cap, U(L.st_cols), &hdr->ctr[CTR_COLS], &hdr->err);
+            if (cols_t)
+                cols_t_kernel<<<split_grid(cols_t_kernel, sm_c, L.max_span_parts), 256, sm_c, s>>>(
+                    bp, U2(L.span_parts), hdr, U(L.rowbase), spans, cap, ranges, d_vals, cap, U(L.st_cols),
+                    &hdr->ctr[CTR_COLS], &hdr->err);
+            else
+                cols_kernel<<<split_grid(cols_kernel, sm_c, L.max_span_parts), 256, sm_c, s>>>(
+                    bp, U2(L.span_parts), hdr, U(L.rowbase), spans, cap, ranges, d_vals, cap, U(L.st_cols),
+                    &hdr->ctr[CTR_COLS], &hdr->err);
             count_launch();
             GS_LAUNCH_CHECK();
             if (d_keys64) {
@@ -1338,7 +1588,7 @@ __global__ void lookback_selftest_kernel(int which, uint32_t *state, uint32_t *e
     if (which == 0) {
         if (threadIdx.x < 32) (void)lookback_scalar(state, 1u, 5u, err, limit);
     } else {
-        (void)lookback_digit(state, 1u, 256, (int)threadIdx.x, err, limit);
+        (void)lookback_digit<kLookWindow>(state, 1u, 256, (int)threadIdx.x, err, limit);
     }
 }
 } // namespace
