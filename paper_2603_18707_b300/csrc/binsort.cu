@@ -516,17 +516,17 @@ compact_kernel(const __grid_constant__ BinPlan bp, const uint32_t *__restrict__ 
 }
 
 // 2. plan (one CTA of 1024 threads): record partitions per camera (kSortTile
-// records each: rec_parts[p] = (camera, chunk)); span count of every padded
+// records each: rec_parts[p] = (camera, chunk, first, end)); span count of every padded
 // row (the inclusive prefix of the row differences: each camera's block sums
 // to zero, so the prefix restarts at every camera) and its first span
 // (rowbase, exclusive prefix over all rows); span partitions per row
-// (kColTile spans each: span_parts[q] = (row | camera << 18, chunk)); the
+// (kColTile spans each: span_parts[q] = (row | camera << 18, chunk, first, end)); the
 // overlap totals and the capacity check.
 __global__ void __launch_bounds__(1024)
 plan_kernel(const __grid_constant__ BinPlan bp, WsHeader *hdr, const uint32_t *__restrict__ seg,
-            uint2 *__restrict__ rec_parts, uint32_t max_rec_parts, const uint32_t *__restrict__ rowdiff,
-            uint32_t *__restrict__ rowbase, uint2 *__restrict__ span_parts, uint32_t max_span_parts,
-            uint32_t span_cap, uint32_t capacity, int ell)
+            uint4 *__restrict__ rec_parts, uint32_t max_rec_parts, const uint32_t *__restrict__ rowdiff,
+            uint32_t *__restrict__ rowbase, uint4 *__restrict__ span_parts, uint32_t max_span_parts,
+            uint32_t *__restrict__ rowq, uint32_t span_cap, uint32_t capacity, int ell)
 {
     __shared__ uint32_t s_cum[kMaxCams + 1];
     __shared__ uint32_t s_warp[32];
@@ -546,7 +546,8 @@ plan_kernel(const __grid_constant__ BinPlan bp, WsHeader *hdr, const uint32_t *_
     for (uint32_t p = tid; p < nrp; p += 1024) {
         int c = 0;
         while (c + 1 < bp.ncam && s_cum[c + 1] <= p) ++c;
-        rec_parts[p] = make_uint2((uint32_t)c, p - s_cum[c]);
+        const uint32_t k = p - s_cum[c], beg = seg[c] + k * kSortTile;
+        rec_parts[p] = make_uint4((uint32_t)c, k, beg, min(seg[c + 1], beg + kSortTile));
     }
     // rows: thread t owns padded rows [g0, g1)
     const int G = bp.G;
@@ -578,13 +579,17 @@ plan_kernel(const __grid_constant__ BinPlan bp, WsHeader *hdr, const uint32_t *_
     uint32_t NQ;
     uint32_t q = block_excl_scan<32>(nq, s_warp, NQ);
     int c = 0;
+    if (tid == 1023) rowq[G] = min(NQ, max_span_parts);
     for (int g = g0; g < g1; ++g) {
         while (c + 1 < bp.ncam && bp.cam[c + 1].gpad <= g) ++c;
+        rowq[g] = min(q, max_span_parts);
         const uint32_t lo = min(rowbase[g], span_cap);
         const uint32_t hi = min(g + 1 == G ? R : rowbase[g + 1], span_cap);
         const uint32_t n = (hi - lo + kColTile - 1) / kColTile;
         for (uint32_t k = 0; k < n; ++k, ++q)
-            if (q < max_span_parts) span_parts[q] = make_uint2((uint32_t)g | ((uint32_t)c << 18), k);
+            if (q < max_span_parts)
+                span_parts[q] = make_uint4((uint32_t)g | ((uint32_t)c << 18), k, lo + k * kColTile,
+                                           min(hi, lo + (k + 1) * kColTile));
     }
     if (tid == 0) {
         hdr->n_span = R;
@@ -600,7 +605,8 @@ plan_kernel(const __grid_constant__ BinPlan bp, WsHeader *hdr, const uint32_t *_
 
 // One Onesweep pass over BITS bits starting at `shift`, over segments: the
 // keys of segment c are [seg[c], seg[c+1]); partition p covers chunk k of
-// segment c, (c, k) = parts[p] (parts == NULL: one segment, chunk p). Keys
+// segment c, keys [first, end): parts[p] = (c, k, first, end) (parts == NULL:
+// one segment, chunk p). Keys
 // move only within their segment. hist + c * hist_stride holds the
 // segment's counts of this pass's digits. Dynamic shared memory: keys,
 // values, per-warp digit counters, two per-digit tables.
@@ -614,7 +620,7 @@ template <int BITS>
 __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) // the pass is latency-bound
 onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                 uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
-                const uint32_t *__restrict__ seg, const uint2 *__restrict__ parts, const uint32_t *nparts_ptr,
+                const uint32_t *__restrict__ seg, const uint4 *__restrict__ parts, const uint32_t *nparts_ptr,
                 int shift, const uint32_t *__restrict__ hist, int hist_stride, uint32_t *state, uint32_t *ctr,
                 uint32_t *err)
 {
@@ -637,11 +643,15 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
     const uint32_t part = *s_part;
     const uint32_t nparts = parts ? *nparts_ptr : (seg[1] - seg[0] + kSortTile - 1) / kSortTile;
     if (part >= nparts) return;
-    const uint2 pc = parts ? parts[part] : make_uint2(0u, part);
-    const uint32_t c = pc.x, chunk = pc.y;
+    uint32_t c = 0, chunk = part, beg, end;
+    if (parts) {
+        const uint4 d = parts[part];
+        c = d.x, chunk = d.y, beg = d.z, end = d.w;
+    } else {
+        beg = seg[0] + part * kSortTile;
+        end = min(seg[1], beg + kSortTile);
+    }
     const uint32_t sbeg = seg[c], send = seg[c + 1];
-    const uint32_t beg = sbeg + chunk * kSortTile;
-    const uint32_t end = min(send, beg + kSortTile);
 
     // warp-striped load: warp w owns keys [beg + 32 I w, beg + 32 I (w + 1)), I = kSortItems
     const uint32_t wbase = beg + warp * (32 * kSortItems);
@@ -744,8 +754,8 @@ inline size_t split_smem(int max_digits) { return sizeof(uint32_t) * (8 * (size_
 // this warp. Span = (record index, first column | last column << 16); a row
 // the ellipse misses (GS_RECT_ELLIPSE) gets an empty span (first > last).
 template <bool ELL>
-__global__ void GS_SPLIT_BOUNDS
-rows_kernel(const __grid_constant__ BinPlan bp, const uint32_t *__restrict__ seg, const uint2 *__restrict__ parts,
+__global__ void __launch_bounds__(256, 2)
+rows_kernel(const __grid_constant__ BinPlan bp, const uint32_t *__restrict__ seg, const uint4 *__restrict__ parts,
             const WsHeader *hdr, const uint32_t *__restrict__ ids, const ushort4 *__restrict__ rects,
             const float4 *__restrict__ rec, uint32_t N, const uint32_t *__restrict__ rowbase,
             uint2 *__restrict__ spans, uint32_t span_cap, uint32_t *state, uint32_t *ctr, uint32_t *err)
@@ -764,10 +774,9 @@ rows_kernel(const __grid_constant__ BinPlan bp, const uint32_t *__restrict__ seg
         __syncthreads();
         const uint32_t part = *s_part;
         if (part >= nparts) break;
-        const uint2 pc = parts[part];
+        const uint4 pc = parts[part];
         const int c = (int)pc.x;
-        const uint32_t chunk = pc.y;
-        const uint32_t beg = seg[c] + chunk * kRowTile, end = min(seg[c + 1], beg + kRowTile);
+        const uint32_t chunk = pc.y, beg = pc.z, end = pc.w;
         const int ty = bp.cam[c].tiles_y, tx = bp.cam[c].tiles_x;
         const uint32_t wb = beg + warp * (32 * kRowItems);
         // a drawn record's rectangle lies inside its camera's tile grid; the
@@ -868,27 +877,26 @@ struct SpanPart {
     int c, y;
     uint32_t chunk, beg, end;
 };
-__device__ __forceinline__ SpanPart span_part(const BinPlan &bp, const uint2 *parts, uint32_t part,
-                                              const uint32_t *rowbase, uint32_t span_cap)
+__device__ __forceinline__ SpanPart span_part(const BinPlan &bp, const uint4 pc)
 {
-    const uint2 pc = parts[part];
     SpanPart s;
     const int g = (int)(pc.x & 0x3ffffu);
     s.c = (int)(pc.x >> 18);
     s.y = g - bp.cam[s.c].gpad;
     s.chunk = pc.y;
-    const uint32_t lo = min(rowbase[g], span_cap), hi = min(rowbase[g + 1], span_cap);
-    s.beg = lo + s.chunk * kColTile;
-    s.end = min(hi, s.beg + kColTile);
+    s.beg = pc.z;
+    s.end = pc.w;
     return s;
 }
 
 // 5. tile counts: per span partition a difference array over the row's
-// columns, added to the tiles' counters.
+// columns; either written as the partition's row of the column-count matrix
+// (colmat[q][x], turned into offsets by col_offsets_kernel) or added to the
+// tiles' counters.
 __global__ void GS_SPLIT_BOUNDS
-cols_count_kernel(const __grid_constant__ BinPlan bp, const uint2 *__restrict__ parts, const WsHeader *hdr,
+cols_count_kernel(const __grid_constant__ BinPlan bp, const uint4 *__restrict__ parts, const WsHeader *hdr,
                   const uint32_t *__restrict__ rowbase, const uint2 *__restrict__ spans, uint32_t span_cap,
-                  uint32_t *__restrict__ tile_cnt, uint32_t *ctr)
+                  uint32_t *__restrict__ tile_cnt, uint32_t *__restrict__ colmat, uint32_t *ctr)
 {
     extern __shared__ uint32_t smem[];
     const int D = bp.max_tx + 1;
@@ -902,7 +910,7 @@ cols_count_kernel(const __grid_constant__ BinPlan bp, const uint2 *__restrict__ 
         __syncthreads();
         const uint32_t part = *s_part;
         if (part >= nparts) break;
-        const SpanPart sp = span_part(bp, parts, part, rowbase, span_cap);
+        const SpanPart sp = span_part(bp, parts[part]);
         const int tx = bp.cam[sp.c].tiles_x;
         const uint32_t end = sp.y < bp.cam[sp.c].tiles_y ? sp.end : sp.beg; // the padding row has no spans
         for (uint32_t i = sp.beg + tid; i < end; i += 256) {
@@ -916,15 +924,46 @@ cols_count_kernel(const __grid_constant__ BinPlan bp, const uint2 *__restrict__ 
         __syncthreads();
         if (tid < 32) {
             uint32_t *tc = tile_cnt + bp.cam[sp.c].tile_base + (uint32_t)sp.y * tx;
+            uint32_t *cm = colmat ? colmat + (size_t)part * bp.max_tx : nullptr;
             uint32_t carry = 0;
             for (int x0 = 0; x0 < tx; x0 += 32) {
                 const int x = x0 + tid;
                 const uint32_t v = warp_incl_scan(x < tx ? s_d[x] : 0u) + carry;
-                if (x < tx && v) atomicAdd(&tc[x], v);
+                if (cm) {
+                    if (x < tx) cm[x] = v;
+                } else if (x < tx && v) {
+                    atomicAdd(&tc[x], v);
+                }
                 carry = __shfl_sync(0xffffffffu, v, 31);
             }
         }
         __syncthreads();
+    }
+}
+
+// 5b. per tile (c, y, x): the exclusive prefix of colmat[q][x] over row
+// (c, y)'s partitions q in order, in place, and the tile's count. One CTA per
+// padded row.
+__global__ void __launch_bounds__(128)
+col_offsets_kernel(const __grid_constant__ BinPlan bp, const uint32_t *__restrict__ rowq,
+                   uint32_t *__restrict__ colmat, uint32_t *__restrict__ tile_cnt)
+{
+    const int g = blockIdx.x;
+    int c = 0;
+    while (c + 1 < bp.ncam && bp.cam[c + 1].gpad <= g) ++c;
+    const int y = g - bp.cam[c].gpad, tx = bp.cam[c].tiles_x;
+    if (y >= bp.cam[c].tiles_y) return; // the padding row
+    const uint32_t q0 = rowq[g], q1 = rowq[g + 1];
+    uint32_t *tc = tile_cnt + bp.cam[c].tile_base + (uint32_t)y * tx;
+    for (int x = threadIdx.x; x < tx; x += 128) {
+        uint32_t acc = 0;
+        for (uint32_t q = q0; q < q1; ++q) {
+            uint32_t *m = colmat + (size_t)q * bp.max_tx + x;
+            const uint32_t v = *m;
+            *m = acc;
+            acc += v;
+        }
+        tc[x] = acc;
     }
 }
 
@@ -968,8 +1007,8 @@ tile_scan_kernel(const uint32_t *__restrict__ tile_cnt, uint32_t T, uint2 *__res
 // partitions (look-back) + in earlier warps + earlier in this warp. Writes
 // the record index there (places at or past the capacity are dropped; the
 // overflow is flagged by the plan).
-__global__ void GS_SPLIT_BOUNDS
-cols_kernel(const __grid_constant__ BinPlan bp, const uint2 *__restrict__ parts, const WsHeader *hdr,
+__global__ void __launch_bounds__(256, 2)
+cols_kernel(const __grid_constant__ BinPlan bp, const uint4 *__restrict__ parts, const WsHeader *hdr,
             const uint32_t *__restrict__ rowbase, const uint2 *__restrict__ spans, uint32_t span_cap,
             const uint2 *__restrict__ ranges, uint32_t *__restrict__ vals, uint32_t cap, uint32_t *state,
             uint32_t *ctr, uint32_t *err)
@@ -988,7 +1027,7 @@ cols_kernel(const __grid_constant__ BinPlan bp, const uint2 *__restrict__ parts,
         __syncthreads();
         const uint32_t part = *s_part;
         if (part >= nparts) break;
-        SpanPart sp = span_part(bp, parts, part, rowbase, span_cap);
+        SpanPart sp = span_part(bp, parts[part]);
         const int tx = bp.cam[sp.c].tiles_x;
         if (sp.y >= bp.cam[sp.c].tiles_y) sp.end = sp.beg; // the padding row has no spans
         const uint32_t wb = sp.beg + warp * (32 * kColItems);
@@ -1075,43 +1114,67 @@ static_assert(kTItems * 256 == kSortTile && kTItems * 256 == kColTile, "partitio
 
 inline size_t tsplit_smem(int max_digits)
 {
-    return sizeof(uint16_t) * 256 * (size_t)max_digits + sizeof(uint32_t) * ((size_t)max_digits + 4);
+    return sizeof(uint16_t) * 256 * (size_t)max_digits + sizeof(uint32_t) * ((size_t)max_digits + 4) + 32;
 }
 
 // cnt[d][0..256) for d < nd: exclusive prefix over the threads in place; the
-// digit's total to tot[d]. Warp w takes digits w, w + 8, ...; lane l holds
-// threads 8 l .. 8 l + 7 (one 16-byte word).
+// digit's total to tot[d]. Warp w takes digits w, w + 8, ..., two at a time
+// (independent chains); lane l holds threads 8 l .. 8 l + 7 (one 16-byte word).
+__device__ __forceinline__ uint32_t tsplit_prefix8(uint4 &q)
+{
+    uint32_t w[4] = {q.x, q.y, q.z, q.w}, v[8], s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[2 * k] = w[k] & 0xffffu;
+        v[2 * k + 1] = w[k] >> 16;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t x = v[k];
+        v[k] = s;
+        s += x;
+    }
+    q = make_uint4(v[0] | (v[1] << 16), v[2] | (v[3] << 16), v[4] | (v[5] << 16), v[6] | (v[7] << 16));
+    return s;
+}
+
+__device__ __forceinline__ uint4 add16x2(uint4 q, uint32_t e)
+{
+    const uint32_t ee = e | (e << 16); // no carries: every sum stays below 2^16
+    return make_uint4(q.x + ee, q.y + ee, q.z + ee, q.w + ee);
+}
+
 __device__ __forceinline__ void tsplit_scan(uint16_t *cnt, uint32_t *tot, int nd)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int d = warp; d < nd; d += 8) {
-        uint4 *row = reinterpret_cast<uint4 *>(cnt + (size_t)d * 256);
-        const uint4 q = row[lane];
-        uint32_t w[4] = {q.x, q.y, q.z, q.w};
-        uint32_t s = 0, v[8];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            v[2 * k] = w[k] & 0xffffu;
-            v[2 * k + 1] = w[k] >> 16;
+    for (int d = warp; d < nd; d += 16) {
+        const int d2 = d + 8;
+        const bool two = d2 < nd;
+        uint4 *r0 = reinterpret_cast<uint4 *>(cnt + (size_t)d * 256);
+        uint4 *r1 = reinterpret_cast<uint4 *>(cnt + (size_t)(two ? d2 : d) * 256);
+        uint4 q0 = r0[lane], q1 = two ? r1[lane] : make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t s0 = tsplit_prefix8(q0), s1 = tsplit_prefix8(q1);
+        const uint32_t i0 = warp_incl_scan(s0), i1 = warp_incl_scan(s1);
+        r0[lane] = add16x2(q0, i0 - s0);
+        if (two) r1[lane] = add16x2(q1, i1 - s1);
+        if (lane == 31) {
+            tot[d] = i0;
+            if (two) tot[d2] = i1;
         }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const uint32_t x = v[k];
-            v[k] = s;
-            s += x;
-        }
-        const uint32_t incl = warp_incl_scan(s);
-        const uint32_t ex = incl - s;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) w[k] = ((v[2 * k] + ex) & 0xffffu) | ((v[2 * k + 1] + ex) << 16);
-        row[lane] = make_uint4(w[0], w[1], w[2], w[3]);
-        if (lane == 31) tot[d] = incl;
     }
 }
 
+// A persistent split kernel claims a partition only when it is ready to
+// process it (a partition claimed early would hold up the look-back of every
+// later one); thread 0 claims it and loads its descriptor for the CTA.
+struct NextPart {
+    uint32_t part;
+    uint4 desc;
+};
+
 template <bool ELL>
 __global__ void __launch_bounds__(256, 2)
-rows_t_kernel(const __grid_constant__ BinPlan bp, const uint32_t *__restrict__ seg, const uint2 *__restrict__ parts,
+rows_t_kernel(const __grid_constant__ BinPlan bp, const uint32_t *__restrict__ seg, const uint4 *__restrict__ parts,
               const WsHeader *hdr, const uint32_t *__restrict__ ids, const ushort4 *__restrict__ rects,
               const float4 *__restrict__ rec, uint32_t N, const uint32_t *__restrict__ rowbase,
               uint2 *__restrict__ spans, uint32_t span_cap, uint32_t *state, uint32_t *ctr, uint32_t *err)
@@ -1120,23 +1183,28 @@ rows_t_kernel(const __grid_constant__ BinPlan bp, const uint32_t *__restrict__ s
     const int ND = bp.max_ty;
     uint16_t *cnt = reinterpret_cast<uint16_t *>(smem); // [ND][256]
     uint32_t *sbase = smem + (size_t)ND * 128;           // [ND]
-    uint32_t *s_part = sbase + ND;
+    NextPart *s_next = reinterpret_cast<NextPart *>(sbase + ((ND + 3) & ~3));
     const int tid = threadIdx.x;
     const uint32_t nparts = hdr->n_rec_parts;
+    uint4 *z = reinterpret_cast<uint4 *>(smem);
     while (true) {
-        {
-            uint4 *z = reinterpret_cast<uint4 *>(smem);
-            for (int i = tid; i < ND * 32; i += 256) z[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (int i = tid; i < ND * 32; i += 256) z[i] = make_uint4(0u, 0u, 0u, 0u);
+        if (tid == 0) {
+            const uint32_t p0 = atomicAdd(ctr, 1u);
+            s_next->part = p0;
+            s_next->desc = p0 < nparts ? parts[p0] : make_uint4(0u, 0u, 0u, 0u);
         }
-        if (tid == 0) *s_part = atomicAdd(ctr, 1u);
         __syncthreads();
-        const uint32_t part = *s_part;
+        const uint32_t part = s_next->part;
         if (part >= nparts) break;
-        const uint2 pc = parts[part];
+        const uint4 pc = s_next->desc;
         const int c = (int)pc.x;
-        const uint32_t chunk = pc.y;
-        const uint32_t beg = seg[c] + chunk * kRowTile, end = min(seg[c + 1], beg + kRowTile);
+        const uint32_t chunk = pc.y, beg = pc.z, end = pc.w;
         const int ty = bp.cam[c].tiles_y, tx = bp.cam[c].tiles_x;
+        const int gp = bp.cam[c].gpad;
+        // this thread's digits' first spans, used after the look-back
+        const uint32_t rb0 = tid < ty ? rowbase[gp + tid] : 0u;
+        const uint32_t rb1 = tid + 256 < ty ? rowbase[gp + tid + 256] : 0u;
         const uint32_t t0 = beg + tid * kTItems;
         uint32_t rid[kTItems], rxr[kTItems], ryr[kTItems];
 #pragma unroll
@@ -1159,9 +1227,11 @@ rows_t_kernel(const __grid_constant__ BinPlan bp, const uint32_t *__restrict__ s
         __syncthreads();
         tsplit_scan(cnt, sbase, ty);
         __syncthreads();
-        const int gp = bp.cam[c].gpad;
-        for (int y = tid; y < ty; y += 256)
-            sbase[y] = rowbase[gp + y] + publish_digit<kSplitWindow>(state, part, chunk, bp.max_ty, y, sbase[y], err);
+        if (tid < ty)
+            sbase[tid] = rb0 + publish_digit<kSplitWindow>(state, part, chunk, bp.max_ty, tid, sbase[tid], err);
+        if (tid + 256 < ty)
+            sbase[tid + 256] =
+                rb1 + publish_digit<kSplitWindow>(state, part, chunk, bp.max_ty, tid + 256, sbase[tid + 256], err);
         __syncthreads();
         const int W = bp.cam[c].W, H = bp.cam[c].H;
 #pragma unroll
@@ -1194,30 +1264,38 @@ rows_t_kernel(const __grid_constant__ BinPlan bp, const uint32_t *__restrict__ s
 }
 
 __global__ void GS_SPLIT_BOUNDS
-cols_t_kernel(const __grid_constant__ BinPlan bp, const uint2 *__restrict__ parts, const WsHeader *hdr,
+cols_t_kernel(const __grid_constant__ BinPlan bp, const uint4 *__restrict__ parts, const WsHeader *hdr,
               const uint32_t *__restrict__ rowbase, const uint2 *__restrict__ spans, uint32_t span_cap,
-              const uint2 *__restrict__ ranges, uint32_t *__restrict__ vals, uint32_t cap, uint32_t *state,
-              uint32_t *ctr, uint32_t *err)
+              const uint32_t *__restrict__ colmat, const uint2 *__restrict__ ranges, uint32_t *__restrict__ vals,
+              uint32_t cap, uint32_t *state, uint32_t *ctr, uint32_t *err)
 {
     extern __shared__ uint32_t smem[];
     const int ND = bp.max_tx;
     uint16_t *cnt = reinterpret_cast<uint16_t *>(smem); // [ND][256]
     uint32_t *sbase = smem + (size_t)ND * 128;           // [ND]
-    uint32_t *s_part = sbase + ND;
+    NextPart *s_next = reinterpret_cast<NextPart *>(sbase + ((ND + 3) & ~3));
     const int tid = threadIdx.x;
     const uint32_t nparts = hdr->n_span_parts;
+    uint4 *z = reinterpret_cast<uint4 *>(smem);
     while (true) {
-        {
-            uint4 *z = reinterpret_cast<uint4 *>(smem);
-            for (int i = tid; i < ND * 32; i += 256) z[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (int i = tid; i < ND * 32; i += 256) z[i] = make_uint4(0u, 0u, 0u, 0u);
+        if (tid == 0) {
+            const uint32_t p0 = atomicAdd(ctr, 1u);
+            s_next->part = p0;
+            s_next->desc = p0 < nparts ? parts[p0] : make_uint4(0u, 0u, 0u, 0u);
         }
-        if (tid == 0) *s_part = atomicAdd(ctr, 1u);
         __syncthreads();
-        const uint32_t part = *s_part;
+        const uint32_t part = s_next->part;
         if (part >= nparts) break;
-        SpanPart sp = span_part(bp, parts, part, rowbase, span_cap);
+        SpanPart sp = span_part(bp, s_next->desc);
         const int tx = bp.cam[sp.c].tiles_x;
         if (sp.y >= bp.cam[sp.c].tiles_y) sp.end = sp.beg; // the padding row has no spans
+        const uint32_t trow = (uint32_t)bp.cam[sp.c].tile_base + (uint32_t)sp.y * tx;
+        // this thread's digits' first places: the tile's start, plus with the
+        // column-count matrix the counts of the row's earlier partitions
+        const uint32_t *cm = colmat ? colmat + (size_t)part * bp.max_tx : nullptr;
+        const uint32_t tb0 = tid < tx ? ranges[trow + tid].x + (cm ? cm[tid] : 0u) : 0u;
+        const uint32_t tb1 = tid + 256 < tx ? ranges[trow + tid + 256].x + (cm ? cm[tid + 256] : 0u) : 0u;
         const uint32_t t0 = sp.beg + tid * kTItems;
         uint32_t sid[kTItems], sxr[kTItems];
 #pragma unroll
@@ -1236,9 +1314,16 @@ cols_t_kernel(const __grid_constant__ BinPlan bp, const uint2 *__restrict__ part
         __syncthreads();
         tsplit_scan(cnt, sbase, tx);
         __syncthreads();
-        const uint32_t trow = (uint32_t)bp.cam[sp.c].tile_base + (uint32_t)sp.y * tx;
-        for (int x = tid; x < tx; x += 256)
-            sbase[x] = ranges[trow + x].x + publish_digit<kSplitWindow>(state, part, sp.chunk, bp.max_tx, x, sbase[x], err);
+        if (cm) {
+            if (tid < tx) sbase[tid] = tb0;
+            if (tid + 256 < tx) sbase[tid + 256] = tb1;
+        } else {
+            if (tid < tx)
+                sbase[tid] = tb0 + publish_digit<kSplitWindow>(state, part, sp.chunk, bp.max_tx, tid, sbase[tid], err);
+            if (tid + 256 < tx)
+                sbase[tid + 256] = tb1 + publish_digit<kSplitWindow>(state, part, sp.chunk, bp.max_tx, tid + 256,
+                                                                     sbase[tid + 256], err);
+        }
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < kTItems; ++j) {
@@ -1273,7 +1358,7 @@ keys64_kernel(const uint2 *__restrict__ ranges, uint32_t T, const uint32_t *__re
 
 struct WsLayout {
     size_t hdr, hist, rowdiff, seg, st_compact, st_depth, st_rows, st_cols, st_scan, tile_cnt, zero_end;
-    size_t rowbase, rec_parts, span_parts, dk0, dk1, dv0, dv1, spans, total;
+    size_t rowbase, rowq, rec_parts, span_parts, colmat, dk0, dk1, dv0, dv1, spans, total;
     uint32_t max_rec_parts, max_span_parts;
     size_t st_depth_stride; // uint32 entries per pass
 };
@@ -1298,8 +1383,10 @@ WsLayout ws_layout(const BinPlan &bp, int64_t N, int64_t cap, int64_t total_tile
     L.tile_cnt = take(sizeof(uint32_t) * total_tiles);
     L.zero_end = o;
     L.rowbase = take(sizeof(uint32_t) * (bp.G + 1));
-    L.rec_parts = take(sizeof(uint2) * L.max_rec_parts);
-    L.span_parts = take(sizeof(uint2) * L.max_span_parts);
+    L.rowq = take(sizeof(uint32_t) * (bp.G + 1));
+    L.rec_parts = take(sizeof(uint4) * L.max_rec_parts);
+    L.span_parts = take(sizeof(uint4) * L.max_span_parts);
+    L.colmat = take(bp.max_tx <= kThreadDigits ? sizeof(uint32_t) * (size_t)bp.max_tx * L.max_span_parts : 0);
     L.dk0 = take(sizeof(uint32_t) * N + 16);
     L.dk1 = take(sizeof(uint32_t) * N);
     L.dv0 = take(sizeof(uint32_t) * N);
@@ -1352,7 +1439,7 @@ cudaError_t smem_optin(K kernel, size_t bytes, bool *done)
 
 template <int BITS>
 cudaError_t launch_onesweep(unsigned grid, cudaStream_t s, const uint32_t *ki, const uint32_t *vi,
-                            uint32_t *ko, uint32_t *vo, const uint32_t *seg, const uint2 *parts,
+                            uint32_t *ko, uint32_t *vo, const uint32_t *seg, const uint4 *parts,
                             const uint32_t *nparts, int shift, const uint32_t *hist, int hist_stride,
                             uint32_t *state, uint32_t *ctr, uint32_t *err)
 {
@@ -1426,6 +1513,7 @@ extern "C" gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t nc
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws + L.hdr);
     auto U = [&](size_t off) { return reinterpret_cast<uint32_t *>(ws + off); };
     auto U2 = [&](size_t off) { return reinterpret_cast<uint2 *>(ws + off); };
+    auto U4 = [&](size_t off) { return reinterpret_cast<uint4 *>(ws + off); };
     uint2 *ranges = reinterpret_cast<uint2 *>(d_ranges);
     const uint32_t T = (uint32_t)t.total_tiles;
     const uint32_t cap = (uint32_t)capacity;
@@ -1445,14 +1533,15 @@ extern "C" gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t nc
         count_launch();
         GS_LAUNCH_CHECK();
         // 2. plan
-        plan_kernel<<<1, 1024, 0, s>>>(bp, hdr, U(L.seg), U2(L.rec_parts), L.max_rec_parts, U(L.rowdiff),
-                                       U(L.rowbase), U2(L.span_parts), L.max_span_parts, cap, cap, ell ? 1 : 0);
+        plan_kernel<<<1, 1024, 0, s>>>(bp, hdr, U(L.seg), U4(L.rec_parts), L.max_rec_parts, U(L.rowdiff),
+                                       U(L.rowbase), U4(L.span_parts), L.max_span_parts, U(L.rowq), cap, cap,
+                                       ell ? 1 : 0);
         count_launch();
         GS_LAUNCH_CHECK();
         // 3. depth sort within each camera, 4 passes ping-pong: result back in (dk0, dv0)
         uint32_t *kin = U(L.dk0), *vin = U(L.dv0), *kout = U(L.dk1), *vout = U(L.dv1);
         for (int p = 0; p < 4; ++p) {
-            if (launch_onesweep<8>(L.max_rec_parts, s, kin, vin, kout, vout, U(L.seg), U2(L.rec_parts),
+            if (launch_onesweep<8>(L.max_rec_parts, s, kin, vin, kout, vout, U(L.seg), U4(L.rec_parts),
                                    &hdr->n_rec_parts, 8 * p, U(L.hist) + 256 * p, 1024,
                                    U(L.st_depth) + p * L.st_depth_stride, &hdr->ctr[CTR_DEPTH + p],
                                    &hdr->err) != cudaSuccess) {
@@ -1490,7 +1579,7 @@ extern "C" gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t nc
                 return GS_ERR_CUDA;
             }
 #define GS_ROWS_ARGS                                                                                           \
-    bp, U(L.seg), U2(L.rec_parts), hdr, vin, sp.rect, sp.rec, (uint32_t)N, U(L.rowbase), spans, cap, U(L.st_rows), \
+    bp, U(L.seg), U4(L.rec_parts), hdr, vin, sp.rect, sp.rec, (uint32_t)N, U(L.rowbase), spans, cap, U(L.st_rows), \
         &hdr->ctr[CTR_ROWS], &hdr->err
             if (rows_t && ell)
                 rows_t_kernel<true><<<gr, 256, sm_r, s>>>(GS_ROWS_ARGS);
@@ -1503,7 +1592,8 @@ extern "C" gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t nc
 #undef GS_ROWS_ARGS
             count_launch();
             GS_LAUNCH_CHECK();
-            // 5. tile counts
+            // 5. tile counts, 6. tile ranges, 7. column split into the tiles' lists
+            const bool use_colmat = cols_t; // column offsets from the count matrix, no look-back
             const size_t sm_cc = split_smem(bp.max_tx);
             const size_t sm_c = cols_t ? tsplit_smem(bp.max_tx) : sm_cc;
             if (smem_optin(cols_count_kernel, smw_max, optin_cc) != cudaSuccess ||
@@ -1513,22 +1603,26 @@ extern "C" gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t nc
                 return GS_ERR_CUDA;
             }
             cols_count_kernel<<<split_grid(cols_count_kernel, sm_cc, L.max_span_parts), 256, sm_cc, s>>>(
-                bp, U2(L.span_parts), hdr, U(L.rowbase), spans, cap, U(L.tile_cnt), &hdr->ctr[CTR_COUNT_COLS]);
+                bp, U4(L.span_parts), hdr, U(L.rowbase), spans, cap, U(L.tile_cnt), use_colmat ? U(L.colmat) : nullptr,
+                &hdr->ctr[CTR_COUNT_COLS]);
             count_launch();
             GS_LAUNCH_CHECK();
-            // 6. tile ranges
+            if (use_colmat) {
+                col_offsets_kernel<<<bp.G, 128, 0, s>>>(bp, U(L.rowq), U(L.colmat), U(L.tile_cnt));
+                count_launch();
+                GS_LAUNCH_CHECK();
+            }
             tile_scan_kernel<<<(T + kScanTile - 1) / kScanTile, 256, 0, s>>>(U(L.tile_cnt), T, ranges, cap, hdr,
                                                                             U(L.st_scan));
             count_launch();
             GS_LAUNCH_CHECK();
-            // 7. column split into the tiles' lists
             if (cols_t)
                 cols_t_kernel<<<split_grid(cols_t_kernel, sm_c, L.max_span_parts), 256, sm_c, s>>>(
-                    bp, U2(L.span_parts), hdr, U(L.rowbase), spans, cap, ranges, d_vals, cap, U(L.st_cols),
-                    &hdr->ctr[CTR_COLS], &hdr->err);
+                    bp, U4(L.span_parts), hdr, U(L.rowbase), spans, cap, U(L.colmat), ranges, d_vals, cap,
+                    U(L.st_cols), &hdr->ctr[CTR_COLS], &hdr->err);
             else
                 cols_kernel<<<split_grid(cols_kernel, sm_c, L.max_span_parts), 256, sm_c, s>>>(
-                    bp, U2(L.span_parts), hdr, U(L.rowbase), spans, cap, ranges, d_vals, cap, U(L.st_cols),
+                    bp, U4(L.span_parts), hdr, U(L.rowbase), spans, cap, ranges, d_vals, cap, U(L.st_cols),
                     &hdr->ctr[CTR_COLS], &hdr->err);
             count_launch();
             GS_LAUNCH_CHECK();
