@@ -77,27 +77,42 @@ def hbm_peak_gbs() -> tuple[float, str]:
         return 6400.0, "fallback 6.4 TB/s"
 
 
+def _row_spans(p) -> int:
+    """Row spans of one gs_bin_sort call: the tile rows each drawn record's
+    rectangle covers, summed (read from the record buffer, layout of
+    gs_splat2d_bytes in include/gs.h)."""
+    import torch
+    N = p.ncam * p.P
+    a256 = lambda x: (x + 255) // 256 * 256
+    o = a256(48 * N)
+    rect = p.splat2d[o:o + 8 * N].view(torch.int16).view(N, 4).to(torch.int32) & 0xFFFF
+    tiles = p.splat2d[o + a256(8 * N):o + a256(8 * N) + 4 * N].view(torch.int32)
+    rows = (rect[:, 3] - rect[:, 1] + 1) * (tiles > 0)
+    return int(rows.sum().item())
+
+
 def binsort_bytes(r) -> dict:
     """Algorithmic DRAM bytes of one gs_bin_sort call per camera set, from
-    its record and overlap counts: compaction reads the tile count of every
-    record (4 B) and the depth key of every drawn one (4 B) and writes
-    (key, id) (8 B); four 8-bit depth passes read and write 16 B per drawn
-    record each; emission reads the id (4 B) and the tile rectangle (8 B,
-    whose area is the tile count) per drawn record and writes (tile, id)
-    (8 B) per overlap;
-    each tile pass reads and writes 16 B per overlap; the ranges kernel
-    reads 4 B per overlap and writes 8 B per tile. For comparison, the
-    3DGS design (one LSD sort of 64-bit (tile | depth) keys with 32-bit
-    ids) moves 8 B (key write) + 24 B per 8-bit pass per overlap."""
+    its record, row-span and overlap counts: compaction reads the tile count
+    of every record (4 B) and the depth key and tile rectangle of every
+    drawn one (4 + 8 B) and writes (key, id) (8 B); four 8-bit depth passes
+    read and write 16 B per drawn record each; the row split reads the id
+    and the rectangle (12 B) per drawn record and writes 8 B per row span;
+    the tile counts read 8 B per span; the column split reads 8 B per span
+    and writes the 4-byte record index per overlap; the tile scan reads 4 B
+    and writes 8 B per tile. For comparison, the 3DGS design (one LSD sort
+    of 64-bit (tile | depth) keys with 32-bit ids) moves 8 B (key write) +
+    24 B per 8-bit pass per overlap."""
     ours = ref = 0
+    spans = 0
     for p in getattr(r, "parts", [r]):
         drawn, over = p.n_records()
+        R = _row_spans(p)
+        spans += R
         bits = max(1, (p.total_tiles - 1).bit_length())
-        tile_passes = max(1, (bits + 8) // 9)
-        ours += (4 * p.ncam * p.P + (12 + 4 * 16 + 12) * drawn
-                 + (8 + 16 * tile_passes + 4) * over + 8 * p.total_tiles)
+        ours += 4 * p.ncam * p.P + (20 + 4 * 16 + 12) * drawn + (8 + 8 + 8) * R + 4 * over + 12 * p.total_tiles
         ref += (12 + 24 * math.ceil((bits + 32) / 8)) * over
-    return {"ours": ours, "3dgs_design": ref}
+    return {"ours": ours, "3dgs_design": ref, "row_spans": spans}
 
 
 def load_scene(a, P: int, seed: int = 0):
@@ -167,8 +182,9 @@ def parse():
                         "the generator's order")
     p.add_argument("--upload-streams", type=int, default=1,
                    help="copy streams the end-to-end leg splits each step's upload over")
-    p.add_argument("--groups", type=int, default=2,
-                   help="camera sets issued on streams of their own (1: one stream)")
+    p.add_argument("--groups", type=int, default=1,
+                   help="camera sets issued on streams of their own (1: one stream, the fastest since "
+                        "the binning's persistent kernels fill the GPU)")
     p.add_argument("--ppt", type=int, default=None, help="pixels per blend thread (1, 2, 4)")
     p.add_argument("--tile", type=str, default=None, help="tile shape WxH, e.g. 16x16")
     p.add_argument("--rect", choices=["aabb", "circle", "ellipse"], default=None,
@@ -553,7 +569,9 @@ def run_ours(a, world, rank, local):
                 "frac": sb["ours"] / sort_s / 1e9 / hbm, "peak_gbs": hbm, "peak_source": hbm_src,
                 "bytes_3dgs_design": sb["3dgs_design"],
                 "gbs_3dgs_design_equivalent": sb["3dgs_design"] / sort_s / 1e9,
-                "note": "bound by look-back and ranking latency, not bandwidth (ncu: 16 % DRAM)"}
+                "row_spans_per_step": sb["row_spans"],
+                "note": "the split kernels scatter and gather single 4-8 byte items: bound by L1 lines per "
+                        "cycle and latency, not DRAM bandwidth"}
 
     # roofline of the dominant kernel: the blend, bound by the FP32 pipes
     st = stages["poly1"]
