@@ -99,9 +99,23 @@ __device__ __forceinline__ float2 alpha_pair_h2(float ua, float ub, __half2 v2h,
 // TRACK: keep each pixel's last contributor and evaluation count (only when
 // the caller asks for d_last or d_n_eval: the reverse pass and the
 // evaluation count need them, the image does not)
+// Compaction of the still-active pixel runs between batches (GS_BLEND_COMPACT):
+// per entry only about a sixth of a tile's pixels are still evaluated on the
+// benchmark scene (most have stopped, T < t_min), yet a warp walks the list
+// while any of its lanes holds an active run. When the active runs of a tile
+// fit in fewer warps than hold runs, the runs whose pixels have all stopped
+// write their pixels, the active runs move (through the batch's shared
+// staging buffer, free between batches) into the lowest threads, and the
+// warps left without a run skip the entries of every later batch. The
+// arithmetic per pixel and its order are unchanged: images are bit-identical.
+#ifndef GS_BLEND_COMPACT
+#define GS_BLEND_COMPACT 1
+#endif
+
 template <int KIND, int PPT, bool HALF, bool TRACK>
 __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &cfg, const RenderArgs &g,
-                                            int gtile, float4 *s_a, float4 *s_b, float4 *s_c, uint4 *s_h)
+                                            int gtile, float4 *s_a, float4 *s_b, float4 *s_c, uint4 *s_h,
+                                            float *s_x, uint32_t *s_wc)
 {
     int c = 0;
     while (c + 1 < cams.ncam && cams.cam[c + 1].tile_base <= gtile) ++c;
@@ -109,11 +123,14 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
     const int lt = gtile - cm.tile_base;
     const int tx = lt % cm.tiles_x, ty = lt / cm.tiles_x;
     const int tpr = cfg.tile_w / PPT; // threads per tile row
-    const int lx = ((int)threadIdx.x % tpr) * PPT, ly = (int)threadIdx.x / tpr;
+    // this thread's run of PPT pixels (tile-local first column and row); it
+    // can change at a compaction
+    int lx = ((int)threadIdx.x % tpr) * PPT, ly = (int)threadIdx.x / tpr;
     const float ox = (float)(tx * cfg.tile_w), oy = (float)(ty * cfg.tile_h);
-    const int px0 = tx * cfg.tile_w + lx, py = ty * cfg.tile_h + ly;
-    const float y = ly + 0.5f;
-    const float xmid = lx + 0.5f * PPT; // centre of the thread's run of pixel centres
+    int px0 = tx * cfg.tile_w + lx, py = ty * cfg.tile_h + ly;
+    float y = ly + 0.5f;
+    float xmid = lx + 0.5f * PPT; // centre of the thread's run of pixel centres
+    bool own = true;                // this thread holds a run whose pixels it writes
     const uint2 rg = g.ranges[gtile];
     // an empty or inverted range (only possible after a timed-out sort wait)
     // reads nothing: every range gs_bin_sort writes lies within its output
@@ -152,8 +169,88 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
     // never skips an entry a pixel takes (the FP16x2 path takes the FP32
     // path's decisions, so the same test serves both)
     const float eps_skip = eps * (1.f - 1.f / 1024.f);
+    // the run's pixels to the outputs
+    auto write_run = [&]() {
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+            if (px0 + k < cm.W && py < cm.H) {
+                const int64_t pix = cm.pix_base + (int64_t)py * cm.W + px0 + k;
+                g.out[3 * pix + 0] = fmaf(T[k], g.bg0, C0[k]);
+                g.out[3 * pix + 1] = fmaf(T[k], g.bg1, C1[k]);
+                g.out[3 * pix + 2] = fmaf(T[k], g.bg2, C2[k]);
+                if (g.final_T) g.final_T[pix] = T[k];
+                if (TRACK && g.last) g.last[pix] = lastc[k];
+                if (TRACK && g.n_eval) g.n_eval[pix] = ne[k];
+            }
+        }
+    };
+    // words of a run in the exchange: position, active bits, T and colour
+    // per pixel (+ last contributor and evaluation count)
+    constexpr int XW = 2 + 4 * PPT + (TRACK ? 2 * PPT : 0);
+    const bool can_compact = GS_BLEND_COMPACT && XW * nthreads <= 3 * kMaxBatch * 4 && nthreads % 32 == 0;
+    int alive = (nthreads + 31) >> 5; // warps that hold runs
     for (uint32_t base = 0; base < n; base += B) {
-        if (__syncthreads_count(active != 0) == 0) break;
+        const int nact = __syncthreads_count(active != 0);
+        if (nact == 0) break;
+        if (can_compact && ((nact + 31) >> 5) < alive) {
+            // the batch's staging buffer is free: every thread has left the
+            // previous batch (barrier above) and the next is not staged yet
+            if (own && !active) {
+                write_run();
+                own = false;
+            }
+            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+            const unsigned bal = __ballot_sync(0xffffffffu, active != 0);
+            if (lane == 0) s_wc[wid] = __popc(bal);
+            __syncthreads();
+            int rank = __popc(bal & ((1u << lane) - 1u));
+            for (int w = 0; w < wid; ++w) rank += (int)s_wc[w];
+            if (active) {
+                float *d = s_x + rank;
+                d[0] = __int_as_float(lx | (ly << 16));
+                d[nthreads] = __uint_as_float(active);
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    d[(2 + 4 * k) * nthreads] = T[k];
+                    d[(3 + 4 * k) * nthreads] = C0[k];
+                    d[(4 + 4 * k) * nthreads] = C1[k];
+                    d[(5 + 4 * k) * nthreads] = C2[k];
+                    if (TRACK) {
+                        d[(2 + 4 * PPT + 2 * k) * nthreads] = __uint_as_float(lastc[k]);
+                        d[(3 + 4 * PPT + 2 * k) * nthreads] = __uint_as_float(ne[k]);
+                    }
+                }
+            }
+            __syncthreads();
+            own = (int)threadIdx.x < nact;
+            active = 0;
+            if (own) {
+                const float *d = s_x + threadIdx.x;
+                const int pos = __float_as_int(d[0]);
+                lx = pos & 0xffff;
+                ly = pos >> 16;
+                active = __float_as_uint(d[nthreads]);
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    T[k] = d[(2 + 4 * k) * nthreads];
+                    C0[k] = d[(3 + 4 * k) * nthreads];
+                    C1[k] = d[(4 + 4 * k) * nthreads];
+                    C2[k] = d[(5 + 4 * k) * nthreads];
+                    if (TRACK) {
+                        lastc[k] = __float_as_uint(d[(2 + 4 * PPT + 2 * k) * nthreads]);
+                        ne[k] = __float_as_uint(d[(3 + 4 * PPT + 2 * k) * nthreads]);
+                    }
+                }
+                px0 = tx * cfg.tile_w + lx;
+                py = ty * cfg.tile_h + ly;
+                y = ly + 0.5f;
+                xmid = lx + 0.5f * PPT;
+            }
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) xs[k] = (active >> k & 1u) ? lx + k + 0.5f : NAN;
+            alive = (nact + 31) >> 5;
+            __syncthreads(); // the exchange is read before the batch is staged over it
+        }
         for (int i = threadIdx.x; i < B; i += nthreads) {
             if (base + i < n) {
                 uint32_t v = g.vals[rg.x + base + i];
@@ -316,18 +413,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
             }
         }
     }
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        if (px0 + k < cm.W && py < cm.H) {
-            const int64_t pix = cm.pix_base + (int64_t)py * cm.W + px0 + k;
-            g.out[3 * pix + 0] = fmaf(T[k], g.bg0, C0[k]);
-            g.out[3 * pix + 1] = fmaf(T[k], g.bg1, C1[k]);
-            g.out[3 * pix + 2] = fmaf(T[k], g.bg2, C2[k]);
-            if (g.final_T) g.final_T[pix] = T[k];
-            if (TRACK && g.last) g.last[pix] = lastc[k];
-            if (TRACK && g.n_eval) g.n_eval[pix] = ne[k];
-        }
-    }
+    if (own) write_run();
 }
 
 template <int KIND, int PPT, bool HALF, bool TRACK>
@@ -335,11 +421,11 @@ __global__ void __launch_bounds__(256, GS_RENDER_MIN_BLOCKS)
 render_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
               const __grid_constant__ RenderArgs g)
 {
-    __shared__ float4 s_a[kMaxBatch];
-    __shared__ float4 s_b[kMaxBatch];
-    __shared__ float4 s_c[kMaxBatch];
+    __shared__ float4 s_stage[3 * kMaxBatch]; // the batch's coefficients; between batches the run exchange
     __shared__ uint4 s_h[HALF ? kMaxBatch : 1];
-    render_tile<KIND, PPT, HALF, TRACK>(cams, cfg, g, blockIdx.x, s_a, s_b, s_c, s_h);
+    __shared__ uint32_t s_wc[8];
+    render_tile<KIND, PPT, HALF, TRACK>(cams, cfg, g, blockIdx.x, s_stage, s_stage + kMaxBatch,
+                                        s_stage + 2 * kMaxBatch, s_h, reinterpret_cast<float *>(s_stage), s_wc);
 }
 
 template <int KIND, int PPT, bool HALF, bool TRACK>
@@ -347,10 +433,9 @@ __global__ void __launch_bounds__(256, GS_RENDER_MIN_BLOCKS)
 render_persistent_kernel(const __grid_constant__ CamTable cams, const __grid_constant__ CfgDev cfg,
                          const __grid_constant__ RenderArgs g, uint32_t *work)
 {
-    __shared__ float4 s_a[kMaxBatch];
-    __shared__ float4 s_b[kMaxBatch];
-    __shared__ float4 s_c[kMaxBatch];
+    __shared__ float4 s_stage[3 * kMaxBatch]; // the batch's coefficients; between batches the run exchange
     __shared__ uint4 s_h[HALF ? kMaxBatch : 1];
+    __shared__ uint32_t s_wc[8];
     __shared__ uint32_t s_tile;
     while (true) {
         if (threadIdx.x == 0) s_tile = atomicAdd(work, 1u);
@@ -358,7 +443,8 @@ render_persistent_kernel(const __grid_constant__ CamTable cams, const __grid_con
         const uint32_t t = s_tile;
         __syncthreads(); // every thread has read s_tile before it is overwritten
         if (t >= (uint32_t)cams.total_tiles) break;
-        render_tile<KIND, PPT, HALF, TRACK>(cams, cfg, g, (int)t, s_a, s_b, s_c, s_h);
+        render_tile<KIND, PPT, HALF, TRACK>(cams, cfg, g, (int)t, s_stage, s_stage + kMaxBatch,
+                                            s_stage + 2 * kMaxBatch, s_h, reinterpret_cast<float *>(s_stage), s_wc);
     }
 }
 
