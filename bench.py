@@ -61,9 +61,9 @@ def blend_source_hash() -> str:
 #       python bench.py --profile poly1 --steps 2 --warmup 1
 # and pipe utilisation from a --set full capture of the same kernel (1M
 # splats x 4 cameras; the kernel's code, not the scene, sets these).
-BLEND_CAPTURE = {"src_hash": "2bb33d95d4950f21", "traffic": 732036608 + 499431680,
-                 "ncu": {"issue_active": 0.801, "fma_pipe": 0.321, "alu_pipe": 0.465, "lanes_active_of_32": 16.54,
-                         "warps_active": 0.477,
+BLEND_CAPTURE = {"src_hash": "c75510a148f1422c", "traffic": 731158272 + 499649024,
+                 "ncu": {"issue_active": 0.787, "fma_pipe": 0.335, "alu_pipe": 0.401, "lanes_active_of_32": 17.24,
+                         "warps_active": 0.476,
                          "source": "ncu --set full, render_persistent_kernel<POLY1, 4, FP32, no index tracking>, 1M splats x 4 cameras"}}
 
 
