@@ -254,7 +254,7 @@ gs_status gs_render_backward(void *stream, const gs_camera *cams, int32_t ncam, 
  * Same arguments, results and errors as gs_bin_sort, minus the workspace: the
  * scratch is one fixed array of GS_NOALLOC_WORKSPACE_BYTES in static device
  * memory, held until the process exits. Sizes whose workspace
- * (gs_bin_sort_workspace_bytes(cams, ncam, P, cfg, capacity): about 18 bytes
+ * (gs_bin_sort_workspace_bytes(cams, ncam, P, cfg, capacity): about 17 bytes
  * per record plus 8 bytes per overlap of capacity) would not fit are
  * rejected with GS_ERR_ARG before anything is launched.
  *  - Set-up happens in the first call on each device: with that device

@@ -109,12 +109,22 @@ def test_border_splats_never_dropped(gs, orc, kind, cull):
     assert np.all(rg[:, :2] <= ro[:, :2]) and np.all(rg[:, 2:] >= ro[:, 2:])
 
 
-@pytest.mark.parametrize("case", ["small3cam", "clusters", "ties"])
+@pytest.mark.parametrize("case", ["small3cam", "clusters", "ties", "wide", "tall"])
 def test_binning_bit_exact(gs, case):
     """Sorted record ids, 64-bit (tile, depth) keys and per-tile ranges equal a
-    CPU stable sort of keys built from the GPU's own rectangles and depths."""
+    CPU stable sort of keys built from the GPU's own rectangles and depths.
+    "wide" / "tall": a frame of 512 tile columns / rows at 8x8 tiles, beyond
+    the 384 of the thread-counter splits (the warp-ranking kernels, the
+    look-back column split and the atomic tile counts run there), and of 256
+    / 128 at the wider tiles."""
     from paper_2603_18707_b300 import synth
-    if case == "small3cam":
+    if case == "wide":
+        raw = synth.scene_uniform(4096, 2)
+        cams = [synth.camera_small(4096, 96), synth.camera_small(128, 128)]
+    elif case == "tall":
+        raw = synth.scene_uniform(4096, 3)
+        cams = [synth.camera_small(96, 4096)]
+    elif case == "small3cam":
         raw = synth.scene_uniform(4096, 0)
         cams = [synth.camera_small(128, 128), synth.camera_small(100, 75),
                 synth.look_at([1.0, -0.5, -3.0], [0, 0, 0], 64, 200)]
