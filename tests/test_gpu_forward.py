@@ -504,3 +504,28 @@ def test_ellipse_binning_drops_only_unreached_tiles(gs, orc, kind, cull):
     ref_t, *_ = orc.render_tiled(sc, oc, _oracle_cfg(orc, kind, cull))
     worst, _, _ = _compare(img, ref_t, margin)
     assert worst < TOL_FP32
+
+
+@pytest.mark.parametrize("shape", ["wide", "tall"])
+def test_ellipse_binning_wide_and_tall_frames(gs, shape):
+    """The ellipse mode on frames of 512 tile columns / rows at 8x8 tiles,
+    where the binning runs its warp-ranking splits (the row split cuts each
+    row's columns to the ellipse there too): the image equals the AABB
+    binning's bit for bit, every list is an order-preserving subsequence of
+    the AABB list, and the keys stay sorted by (tile, depth)."""
+    from paper_2603_18707_b300 import synth
+    raw = synth.scene_uniform(4096, 7)
+    cams = [synth.camera_small(4096, 96)] if shape == "wide" else [synth.camera_small(96, 4096)]
+    Ra = _gpu(gs, raw, cams, "poly1", "opacity", rect="aabb", tile=(8, 8))
+    Re = _gpu(gs, raw, cams, "poly1", "opacity", rect="ellipse", tile=(8, 8))
+    assert torch.equal(Ra.out, Re.out)
+    na, ne = Ra.n_records()[1], Re.n_records()[1]
+    assert 0 < ne < na
+    va, ve = Ra.vals.cpu().numpy(), Re.vals.cpu().numpy()
+    ra = Ra.ranges.cpu().numpy().reshape(-1, 2)
+    re_ = Re.ranges.cpu().numpy().reshape(-1, 2)
+    for t in np.nonzero(re_[:, 1] > re_[:, 0])[0]:
+        it = iter(va[ra[t, 0]:ra[t, 1]].tolist())
+        assert all(x in it for x in ve[re_[t, 0]:re_[t, 1]].tolist()), t
+    k = Re.keys64[:ne].cpu().numpy().view(np.uint64)
+    assert np.all(k[1:] >= k[:-1])
