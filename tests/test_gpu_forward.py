@@ -109,7 +109,7 @@ def test_border_splats_never_dropped(gs, orc, kind, cull):
     assert np.all(rg[:, :2] <= ro[:, :2]) and np.all(rg[:, 2:] >= ro[:, 2:])
 
 
-@pytest.mark.parametrize("case", ["small3cam", "clusters", "ties", "wide", "tall"])
+@pytest.mark.parametrize("case", ["small3cam", "clusters", "ties", "wide", "tall", "many_small"])
 def test_binning_bit_exact(gs, case):
     """Sorted record ids, 64-bit (tile, depth) keys and per-tile ranges equal a
     CPU stable sort of keys built from the GPU's own rectangles and depths.
@@ -118,7 +118,14 @@ def test_binning_bit_exact(gs, case):
     look-back column split and the atomic tile counts run there), and of 256
     / 128 at the wider tiles."""
     from paper_2603_18707_b300 import synth
-    if case == "wide":
+    if case == "many_small":
+        # 12 cameras of 1000 splats: a compaction partition (8192 records)
+        # spans up to 9 cameras; the last camera looks away and draws nothing
+        raw = synth.scene_uniform(1000, 8)
+        cams = [synth.look_at([3.0 * np.sin(a), 0.4, -3.0 * np.cos(a)], [0, 0, 0], 64 + 8 * k, 48 + 4 * k)
+                for k, a in enumerate(np.linspace(0.0, 2.0, 11))]
+        cams.append(synth.look_at([0.0, 0.0, -3.0], [0.0, 0.0, -6.0], 64, 64))
+    elif case == "wide":
         raw = synth.scene_uniform(4096, 2)
         cams = [synth.camera_small(4096, 96), synth.camera_small(128, 128)]
     elif case == "tall":
@@ -142,6 +149,8 @@ def test_binning_bit_exact(gs, case):
         I, keys, ranges = expected_binning(g, cams, tile[0], tile[1], R.P)
         n_vis, n_over = R.n_records()
         assert n_over == I.size and n_vis == int((g["tiles"] > 0).sum())
+        if case == "many_small":
+            assert not (g["tiles"][-R.P:] > 0).any()  # the camera looking away draws nothing
         assert np.array_equal(R.vals[:n_over].cpu().numpy().astype(np.int64), I)
         assert np.array_equal(R.keys64[:n_over].cpu().numpy().view(np.uint64), keys)
         assert np.array_equal(R.ranges.cpu().numpy().astype(np.int64), ranges)
