@@ -618,7 +618,7 @@ constexpr size_t onesweep_smem()
 template <int BITS>
 __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) // the pass is latency-bound
 onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
-                uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
+                uint32_t *__restrict__ keys_out /* NULL: sorted keys not kept */, uint32_t *__restrict__ vals_out,
                 const uint32_t *__restrict__ seg, const uint4 *__restrict__ parts, const uint32_t *nparts_ptr,
                 int shift, const uint32_t *__restrict__ hist, int hist_stride, uint32_t *state, uint32_t *ctr,
                 uint32_t *err)
@@ -734,7 +734,7 @@ onesweep_kernel(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
         const uint32_t d = (key >> shift) & M;
         const uint32_t o = s_goff[d] + i - s_bexcl[d];
         if (o < send) { // always true unless a look-back wait timed out
-            keys_out[o] = key;
+            if (keys_out) keys_out[o] = key;
             vals_out[o] = s_vals[i];
         }
     }
@@ -1540,7 +1540,10 @@ extern "C" gs_status gs_bin_sort(void *stream, const gs_camera *cams, int32_t nc
         // 3. depth sort within each camera, 4 passes ping-pong: result back in (dk0, dv0)
         uint32_t *kin = U(L.dk0), *vin = U(L.dv0), *kout = U(L.dk1), *vout = U(L.dv1);
         for (int p = 0; p < 4; ++p) {
-            if (launch_onesweep<8>(L.max_rec_parts, s, kin, vin, kout, vout, U(L.seg), U4(L.rec_parts),
+            // the last pass writes only the record indices: the splits read
+            // nothing else, and 64-bit keys are gathered by index
+            if (launch_onesweep<8>(L.max_rec_parts, s, kin, vin, p == 3 ? nullptr : kout, vout, U(L.seg),
+                                   U4(L.rec_parts),
                                    &hdr->n_rec_parts, 8 * p, U(L.hist) + 256 * p, 1024,
                                    U(L.st_depth) + p * L.st_depth_stride, &hdr->ctr[CTR_DEPTH + p],
                                    &hdr->err) != cudaSuccess) {
