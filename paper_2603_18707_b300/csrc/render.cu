@@ -111,6 +111,9 @@ __device__ __forceinline__ float2 alpha_pair_h2(float ua, float ub, __half2 v2h,
 #ifndef GS_BLEND_COMPACT
 #define GS_BLEND_COMPACT 1
 #endif
+#ifndef GS_BLEND_PACKED
+#define GS_BLEND_PACKED 1
+#endif
 
 template <int KIND, int PPT, bool HALF, bool TRACK>
 __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &cfg, const RenderArgs &g,
@@ -162,6 +165,11 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
     // the row term v2 below is beta = p0 - t^2 and the pixel's exponent /
     // alpha is beta - s^2
     constexpr bool FOLD = !HALF && folds_p1<KIND>();
+    // packed pixel pairs (GS_BLEND_PACKED): the image-only FP32 f1 / exp
+    // blend updates two pixels per FP32x2 instruction, with the signs of
+    // beta, the exponent and the colours flipped so that no operand needs a
+    // negation (the results are bit-identical to the scalar update)
+    constexpr bool PACKED = GS_BLEND_PACKED && FOLD && !TRACK && PPT % 2 == 0;
     // skip threshold of the folded per-run test: 2^-8 below eps (exp: its
     // exponent), far more than the rounding of the run's bound on |s|
     const float fold_skip = KIND == GS_K_EXP ? log2f(eps * (1.f - 1.f / 256.f)) : eps * (1.f - 1.f / 256.f);
@@ -259,7 +267,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                                                           g.rec[3 * (size_t)v + 1], g.rec[3 * (size_t)v + 2], ox, oy);
                 s_a[i] = k.a;
                 s_b[i] = k.b;
-                s_c[i] = k.c;
+                s_c[i] = PACKED ? make_float4(-k.c.x, -k.c.y, -k.c.z, k.c.w) : k.c;
                 if (HALF) {
                     __half2 h[4] = {__float2half2_rn(k.b.y), __float2half2_rn(k.b.z),
                                     __float2half2_rn(k.b.w), __float2half2_rn(k.c.w)};
@@ -279,7 +287,8 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
             const float4 b = s_b[j];
             const float ub = fmaf(a.y, y, a.z);
             const float vv = fmaf(a.w, y, b.x);
-            const float v2 = FOLD ? fmaf(-vv, vv, b.y) : vv * vv; // FOLD: beta
+            // FOLD: beta (PACKED: -beta, exactly, as fma(-x, y, z) = -fma(x, y, -z))
+            const float v2 = PACKED ? fmaf(vv, vv, -b.y) : FOLD ? fmaf(-vv, vv, b.y) : vv * vv;
             const float p3 = (KIND == GS_K_POLY3) ? s_c[j].w : 0.f; // the cubic's top coefficient
             if (PPT > 1 && cfg.monotone) {
                 // smallest Q over this thread's run of pixels: u is affine
@@ -296,7 +305,10 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                 const float ua = fmaf(a.x, lx + 0.5f, ub), uz = fmaf(a.x, lx + PPT - 0.5f, ub);
                 const float um = ((ua > 0.f) != (uz > 0.f)) ? 0.f : fminf(fabsf(ua), fabsf(uz));
 #endif
-                if constexpr (FOLD) {
+                if constexpr (PACKED) {
+                    // the same test on the negated exponent / alpha
+                    if (fmaf(um, um, v2) > -fold_skip) continue;
+                } else if constexpr (FOLD) {
                     // the run's largest exponent / alpha is beta - sm^2
                     if (fmaf(-um, um, v2) < fold_skip) continue;
                 } else if constexpr (KIND == GS_K_POLY1 || KIND == GS_K_EXP) {
@@ -357,6 +369,58 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                     C2[k] = fmaf(col.z, w, C2[k]);
                     T[k] = Tn;
                     if constexpr (TRACK) lastc[k] = pos;
+                }
+            } else if constexpr (PACKED) {
+                // per pixel pair: ne = u^2 - beta = -(exponent / alpha); na
+                // = -min(alpha_max, alpha) where alpha >= eps, else 0 (a
+                // skipped or stopped pixel then keeps T and its colour:
+                // fma(0, T, T) = T); T' = T + na T; the colour gains
+                // (-c)(na T) = c alpha T. Only a pixel that stops takes a
+                // branch (T' < t_min is possible only where alpha >= eps).
+                const float2 ax2 = make_float2(a.x, a.x), ub2 = make_float2(ub, ub), nb2 = make_float2(v2, v2);
+                float na[PPT], Tn[PPT];
+                bool stop = false;
+#pragma unroll
+                for (int k = 0; k < PPT; k += 2) {
+                    const float2 u = __ffma2_rn(ax2, make_float2(xs[k], xs[k + 1]), ub2);
+                    const float2 ne = __ffma2_rn(u, u, nb2);
+                    if constexpr (KIND == GS_K_EXP) {
+                        const float a0 = ex2_approx(-ne.x), a1 = ex2_approx(-ne.y);
+                        na[k] = a0 >= eps ? fmaxf(-a0, -amax) : 0.f;
+                        na[k + 1] = a1 >= eps ? fmaxf(-a1, -amax) : 0.f;
+                    } else {
+                        na[k] = ne.x <= -eps ? fmaxf(ne.x, -amax) : 0.f;
+                        na[k + 1] = ne.y <= -eps ? fmaxf(ne.y, -amax) : 0.f;
+                    }
+                    const float2 T2 = make_float2(T[k], T[k + 1]);
+                    const float2 t = __ffma2_rn(make_float2(na[k], na[k + 1]), T2, T2);
+                    Tn[k] = t.x;
+                    Tn[k + 1] = t.y;
+                    stop |= (t.x < tmin) | (t.y < tmin);
+                }
+                if (stop) {
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) {
+                        if (Tn[k] < tmin) {
+                            na[k] = 0.f;
+                            Tn[k] = T[k];
+                            active &= ~(1u << k);
+                            xs[k] = NAN;
+                        }
+                    }
+                }
+                const float2 cr = make_float2(col.x, col.x), cg = make_float2(col.y, col.y),
+                             cb = make_float2(col.z, col.z);
+#pragma unroll
+                for (int k = 0; k < PPT; k += 2) {
+                    const float2 w = __fmul2_rn(make_float2(na[k], na[k + 1]), make_float2(T[k], T[k + 1]));
+                    const float2 r = __ffma2_rn(cr, w, make_float2(C0[k], C0[k + 1]));
+                    const float2 gg = __ffma2_rn(cg, w, make_float2(C1[k], C1[k + 1]));
+                    const float2 bb = __ffma2_rn(cb, w, make_float2(C2[k], C2[k + 1]));
+                    C0[k] = r.x, C0[k + 1] = r.y;
+                    C1[k] = gg.x, C1[k + 1] = gg.y;
+                    C2[k] = bb.x, C2[k + 1] = bb.y;
+                    T[k] = Tn[k], T[k + 1] = Tn[k + 1];
                 }
             } else {
             float al[PPT];
