@@ -21,6 +21,7 @@
 // tile from an atomic counter until all tiles of all cameras are done (one
 // launch for any mix of resolutions, balanced dynamically).
 #include <algorithm>
+#include <type_traits>
 
 #include <cuda_fp16.h>
 
@@ -30,15 +31,20 @@ namespace gs {
 namespace {
 
 constexpr int kMaxBatch = 256;
+// Image-only f1 / exp blend on packed FP32x2 pixel pairs (see render_tile).
+#ifndef GS_BLEND_PACKED
+#define GS_BLEND_PACKED 1
+#endif
 // Unroll of the per-entry loop (ILP across entries): measured fastest at 4
-// for the polynomial kernels and 8 for exp (0: per kind as measured).
+// for the polynomial kernels, 8 for exp and the packed f1 (0: per kind as
+// measured).
 #ifndef GS_BLEND_UNROLL
 #define GS_BLEND_UNROLL 0
 #endif
 template <int KIND>
 constexpr int blend_unroll()
 {
-    return GS_BLEND_UNROLL ? GS_BLEND_UNROLL : (KIND == GS_K_EXP ? 8 : 4);
+    return GS_BLEND_UNROLL ? GS_BLEND_UNROLL : (KIND == GS_K_EXP || (KIND == GS_K_POLY1 && GS_BLEND_PACKED) ? 8 : 4);
 }
 #ifndef GS_SKIP_MID
 #define GS_SKIP_MID 1 // per-thread skip bound from the run's centre (1) or its two ends (0)
@@ -111,9 +117,6 @@ __device__ __forceinline__ float2 alpha_pair_h2(float ua, float ub, __half2 v2h,
 #ifndef GS_BLEND_COMPACT
 #define GS_BLEND_COMPACT 1
 #endif
-#ifndef GS_BLEND_PACKED
-#define GS_BLEND_PACKED 1
-#endif
 
 template <int KIND, int PPT, bool HALF, bool TRACK>
 __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &cfg, const RenderArgs &g,
@@ -165,11 +168,15 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
     // the row term v2 below is beta = p0 - t^2 and the pixel's exponent /
     // alpha is beta - s^2
     constexpr bool FOLD = !HALF && folds_p1<KIND>();
-    // packed pixel pairs (GS_BLEND_PACKED): the image-only FP32 f1 / exp
-    // blend updates two pixels per FP32x2 instruction, with the signs of
-    // beta, the exponent and the colours flipped so that no operand needs a
-    // negation (the results are bit-identical to the scalar update)
-    constexpr bool PACKED = GS_BLEND_PACKED && FOLD && !TRACK && PPT % 2 == 0;
+    // packed pixel pairs (GS_BLEND_PACKED): the FP32 f1 / exp blend updates
+    // two pixels per FP32x2 instruction, with the signs of beta, the
+    // exponent and the colours flipped so that no operand needs a negation
+    // (the results are bit-identical to the scalar update)
+    constexpr bool PACKED = GS_BLEND_PACKED && FOLD && PPT % 2 == 0;
+    // f1's alpha never exceeds its entry's p0 = o' c0 (beta - s^2 <= beta <=
+    // p0, also as rounded), so a batch whose entries all have p0 <= alpha_max
+    // is walked without the clamp (for the paper's f1, c0 = 0.773: always)
+    constexpr bool NOCLAMP_OK = PACKED && KIND == GS_K_POLY1;
     // skip threshold of the folded per-run test: 2^-8 below eps (exp: its
     // exponent), far more than the rounding of the run's bound on |s|
     const float fold_skip = KIND == GS_K_EXP ? log2f(eps * (1.f - 1.f / 256.f)) : eps * (1.f - 1.f / 256.f);
@@ -259,6 +266,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
             alive = (nact + 31) >> 5;
             __syncthreads(); // the exchange is read before the batch is staged over it
         }
+        bool big = false; // a staged f1 entry with p0 > alpha_max
         for (int i = threadIdx.x; i < B; i += nthreads) {
             if (base + i < n) {
                 uint32_t v = g.vals[rg.x + base + i];
@@ -268,6 +276,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                 s_a[i] = k.a;
                 s_b[i] = k.b;
                 s_c[i] = PACKED ? make_float4(-k.c.x, -k.c.y, -k.c.z, k.c.w) : k.c;
+                if (NOCLAMP_OK) big |= k.b.y > amax;
                 if (HALF) {
                     __half2 h[4] = {__float2half2_rn(k.b.y), __float2half2_rn(k.b.z),
                                     __float2half2_rn(k.b.w), __float2half2_rn(k.c.w)};
@@ -279,8 +288,11 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                 }
             }
         }
-        __syncthreads();
+        const int need_clamp = __syncthreads_or(big);
         const int cnt = (int)min((uint32_t)B, n - base);
+        // the walk over the batch, with or without the alpha_max clamp
+        auto walk = [&](auto clamp_tag) {
+        constexpr bool CLAMP = decltype(clamp_tag)::value;
 #pragma unroll blend_unroll<KIND>()
         for (int j = 0; j < cnt && active; ++j) {
             const float4 a = s_a[j];
@@ -389,8 +401,8 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                         na[k] = a0 >= eps ? fmaxf(-a0, -amax) : 0.f;
                         na[k + 1] = a1 >= eps ? fmaxf(-a1, -amax) : 0.f;
                     } else {
-                        na[k] = ne.x <= -eps ? fmaxf(ne.x, -amax) : 0.f;
-                        na[k + 1] = ne.y <= -eps ? fmaxf(ne.y, -amax) : 0.f;
+                        na[k] = ne.x <= -eps ? (CLAMP ? fmaxf(ne.x, -amax) : ne.x) : 0.f;
+                        na[k + 1] = ne.y <= -eps ? (CLAMP ? fmaxf(ne.y, -amax) : ne.y) : 0.f;
                     }
                     const float2 T2 = make_float2(T[k], T[k + 1]);
                     const float2 t = __ffma2_rn(make_float2(na[k], na[k + 1]), T2, T2);
@@ -406,8 +418,14 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                             Tn[k] = T[k];
                             active &= ~(1u << k);
                             xs[k] = NAN;
+                            if constexpr (TRACK) ne[k] = pos;
                         }
                     }
+                }
+                if constexpr (TRACK) {
+                    // a blended entry has na <= -eps
+#pragma unroll
+                    for (int k = 0; k < PPT; ++k) lastc[k] = na[k] != 0.f ? pos : lastc[k];
                 }
                 const float2 cr = make_float2(col.x, col.x), cg = make_float2(col.y, col.y),
                              cb = make_float2(col.z, col.z);
@@ -475,6 +493,15 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                 }
             }
             }
+        }
+        };
+        if constexpr (NOCLAMP_OK) {
+            if (need_clamp)
+                walk(std::true_type{});
+            else
+                walk(std::false_type{});
+        } else {
+            walk(std::true_type{});
         }
     }
     if (own) write_run();
