@@ -7,8 +7,8 @@
  * Pipeline (one stream, all stream-ordered):
  *   gs_preprocess       project splats into every camera, per-splat support
  *                       threshold and tile rectangle (Eq. 1, Eq. 3-6, Sec. 3.4, App. B)
- *   gs_bin_sort         depth order + tile binning: compaction, radix sorts,
- *                       overlap emission, per-tile ranges
+ *   gs_bin_sort         depth order + tile binning: compaction, depth radix
+ *                       sort, row and column splits, per-tile ranges
  *   gs_render           front-to-back alpha blending per tile (Sec. 2, Eq. 1/2/6)
  *   gs_render_backward  reverse blend + chain rule to the splat inputs (Sec. 4.3)
  * Scene preparation (once per scene, not per frame):
@@ -295,7 +295,7 @@ gs_status gs_workspace_status_async(void *stream, void *d_workspace, uint32_t *d
 /* Self-test of the bounded waits (failure detection without a fault; not
  * part of the rendering path). Runs one of the bounded waits against an
  * event that never comes: which = 0 the scalar decoupled look-back of
- * gs_bin_sort (compaction, emission) against a predecessor partition that
+ * gs_bin_sort (compaction) against a predecessor partition that
  * never publishes its count; which = 1 the per-digit look-back of a radix
  * pass; which = 2 the mbarrier wait of the tcgen05 blend on a barrier that
  * no arrival completes. The wait gives up after spin_limit polls (short
