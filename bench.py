@@ -61,9 +61,9 @@ def blend_source_hash() -> str:
 #       python bench.py --profile poly1 --steps 2 --warmup 1
 # and pipe utilisation from a --set full capture of the same kernel (1M
 # splats x 4 cameras; the kernel's code, not the scene, sets these).
-BLEND_CAPTURE = {"src_hash": "c75510a148f1422c", "traffic": 731158272 + 499649024,
-                 "ncu": {"issue_active": 0.787, "fma_pipe": 0.335, "alu_pipe": 0.401, "lanes_active_of_32": 17.24,
-                         "warps_active": 0.476,
+BLEND_CAPTURE = {"src_hash": "81139881f557cc14", "traffic": 732141056 + 499561472,
+                 "ncu": {"issue_active": 0.753, "fma_pipe": 0.334, "fma_pipe_cycles": 0.452, "alu_pipe": 0.439,
+                         "lanes_active_of_32": 19.89, "warps_active": 0.478,
                          "source": "ncu --set full, render_persistent_kernel<POLY1, 4, FP32, no index tracking>, 1M splats x 4 cameras"}}
 
 
