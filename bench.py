@@ -61,9 +61,9 @@ def blend_source_hash() -> str:
 #       python bench.py --profile poly1 --steps 2 --warmup 1
 # and pipe utilisation from a --set full capture of the same kernel (1M
 # splats x 4 cameras; the kernel's code, not the scene, sets these).
-BLEND_CAPTURE = {"src_hash": "81139881f557cc14", "traffic": 732141056 + 499561472,
-                 "ncu": {"issue_active": 0.753, "fma_pipe": 0.334, "fma_pipe_cycles": 0.452, "alu_pipe": 0.439,
-                         "lanes_active_of_32": 19.89, "warps_active": 0.478,
+BLEND_CAPTURE = {"src_hash": "3adb281604658c0d", "traffic": 731557632 + 499966720,
+                 "ncu": {"issue_active": 0.732, "fma_pipe": 0.317, "fma_pipe_cycles": 0.453, "alu_pipe": 0.409,
+                         "lanes_active_of_32": 18.51, "warps_active": 0.477,
                          "source": "ncu --set full, render_persistent_kernel<POLY1, 4, FP32, no index tracking>, 1M splats x 4 cameras"}}
 
 
@@ -143,7 +143,8 @@ def _default_workload(a) -> bool:
 def fma_peak_tflops(half2: bool) -> float:
     """Measured FFMA (or packed HFMA2) rate of this GPU in TFLOP/s: the
     library's peak microbenchmark, 8 CTAs of 256 threads per SM, timed with
-    CUDA events over three launches after one warm-up launch."""
+    CUDA events over three launches after one warm-up launch; the best of
+    five such timings (single timings varied by up to 7 % between runs)."""
     import torch
     from paper_2603_18707_b300 import api
     sms = torch.cuda.get_device_properties(0).multi_processor_count
@@ -151,12 +152,15 @@ def fma_peak_tflops(half2: bool) -> float:
     sink = torch.empty(blocks * 256, device="cuda", dtype=torch.float32)
     api.gs_fma_peak(half2, blocks, 20, sink)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    flop = sum(api.gs_fma_peak(half2, blocks, 400, sink) for _ in range(3))
-    e1.record()
-    torch.cuda.synchronize()
-    return flop / (e0.elapsed_time(e1) / 1e3) / 1e12
+    best = 0.0
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        flop = sum(api.gs_fma_peak(half2, blocks, 400, sink) for _ in range(3))
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, flop / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    return best
 
 
 def parse():
