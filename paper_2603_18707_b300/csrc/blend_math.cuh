@@ -89,6 +89,8 @@ __device__ __forceinline__ BlendCoef make_coef(const CfgDev &cfg, float4 r0, flo
     // The legacy 3-sigma cut does not bound the eps support, so it never
     // skips.
     if (KIND == GS_K_POLY1 || KIND == GS_K_EXP) p2 = (cfg.cull == GS_CULL_LEGACY3) ? INFINITY : r1.w;
+    // f'2 has no cubic term: its p3 slot carries the cut instead
+    if (KIND == GS_K_POLY2) p3 = (cfg.cull == GS_CULL_LEGACY3) ? INFINITY : r1.w;
     k.b = make_float4(-vy * my, p0, p1, p2);
     k.c = make_float4(r2.x, r2.y, r2.z, p3);
     if constexpr (FOLD) {

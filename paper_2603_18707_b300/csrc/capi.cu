@@ -100,10 +100,17 @@ bool build_cfg(const gs_config *cfg, CfgDev *d)
     // the cubic divided by (Q - x0): c3 (Q - x0)(Q^2 + f3b Q + f3g)
     d->f3r = d->f3b = d->f3g = 0.f;
     d->f3_factored = 0;
+    d->tail_zero = 0;
     if (n == 3 && cfg->c[3] != 0.f) {
         d->f3r = d->x0;
         d->f3b = cfg->c[2] / cfg->c[3] + d->x0;
         d->f3g = cfg->c[1] / cfg->c[3] + d->x0 * d->f3b;
+        // past x0, (Q - x0) > 0, so the cubic stays <= 0 there when c3 < 0
+        // and the quadratic factor has no real root beyond x0 (in double, with
+        // a margin: only then may the blend skip an entry from Q > x0 alone)
+        const double b = d->f3b, g = d->f3g, disc = b * b - 4.0 * g;
+        d->tail_zero = cfg->c[3] < 0.f &&
+                       (disc < 0.0 || (-b + std::sqrt(disc)) / 2.0 < (double)d->x0 * (1.0 - 1e-3));
         // the half form needs the factors inside binary16 range
         d->f3_factored = std::isfinite(d->f3b) && std::isfinite(d->f3g) && fabsf(d->f3b) < 3e4f &&
                          fabsf(d->f3g) < 3e4f && fabsf(d->c[3] * d->x0) < 3e4f;

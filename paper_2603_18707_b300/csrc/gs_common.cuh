@@ -53,6 +53,7 @@ struct CfgDev {
     float h2_band;
     float f3r, f3b, f3g;
     int f3_factored; // 1 when the cubic term is non-zero and the factors are finite
+    int tail_zero;   // f3: the cubic stays <= 0 past its first root x0 (the kernel is 0 there)
 };
 
 // Pointers into the record buffer (see gs_splat2d_bytes).

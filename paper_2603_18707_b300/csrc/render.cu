@@ -31,20 +31,20 @@ namespace gs {
 namespace {
 
 constexpr int kMaxBatch = 256;
-// Image-only f1 / exp blend on packed FP32x2 pixel pairs (see render_tile).
+// FP32 blend on packed FP32x2 pixel pairs (see render_tile).
 #ifndef GS_BLEND_PACKED
 #define GS_BLEND_PACKED 1
 #endif
-// Unroll of the per-entry loop (ILP across entries): measured fastest at 4
-// for the polynomial kernels, 8 for exp and the packed f1 (0: per kind as
-// measured).
+// Unroll of the per-entry loop (ILP across entries): measured fastest at 8
+// for the packed blend of every kernel and for exp, 4 for the scalar
+// polynomial blends (0: per kind as measured).
 #ifndef GS_BLEND_UNROLL
 #define GS_BLEND_UNROLL 0
 #endif
 template <int KIND>
 constexpr int blend_unroll()
 {
-    return GS_BLEND_UNROLL ? GS_BLEND_UNROLL : (KIND == GS_K_EXP || (KIND == GS_K_POLY1 && GS_BLEND_PACKED) ? 8 : 4);
+    return GS_BLEND_UNROLL ? GS_BLEND_UNROLL : (KIND == GS_K_EXP || GS_BLEND_PACKED ? 8 : 4);
 }
 #ifndef GS_SKIP_MID
 #define GS_SKIP_MID 1 // per-thread skip bound from the run's centre (1) or its two ends (0)
@@ -168,11 +168,12 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
     // the row term v2 below is beta = p0 - t^2 and the pixel's exponent /
     // alpha is beta - s^2
     constexpr bool FOLD = !HALF && folds_p1<KIND>();
-    // packed pixel pairs (GS_BLEND_PACKED): the FP32 f1 / exp blend updates
-    // two pixels per FP32x2 instruction, with the signs of beta, the
-    // exponent and the colours flipped so that no operand needs a negation
-    // (the results are bit-identical to the scalar update)
-    constexpr bool PACKED = GS_BLEND_PACKED && FOLD && PPT % 2 == 0;
+    // packed pixel pairs (GS_BLEND_PACKED): the FP32 blend updates two
+    // pixels per FP32x2 instruction, with the signs of the colours (and for
+    // f1 / exp of beta and the exponent, NEGB) flipped so that no operand
+    // needs a negation (the results are bit-identical to the scalar update)
+    constexpr bool PACKED = GS_BLEND_PACKED && !HALF && PPT % 2 == 0;
+    constexpr bool NEGB = PACKED && FOLD;
     // f1's alpha never exceeds its entry's p0 = o' c0 (beta - s^2 <= beta <=
     // p0, also as rounded), so a batch whose entries all have p0 <= alpha_max
     // is walked without the clamp (for the paper's f1, c0 = 0.773: always)
@@ -299,8 +300,8 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
             const float4 b = s_b[j];
             const float ub = fmaf(a.y, y, a.z);
             const float vv = fmaf(a.w, y, b.x);
-            // FOLD: beta (PACKED: -beta, exactly, as fma(-x, y, z) = -fma(x, y, -z))
-            const float v2 = PACKED ? fmaf(vv, vv, -b.y) : FOLD ? fmaf(-vv, vv, b.y) : vv * vv;
+            // FOLD: beta (NEGB: -beta, exactly, as fma(-x, y, z) = -fma(x, y, -z))
+            const float v2 = NEGB ? fmaf(vv, vv, -b.y) : FOLD ? fmaf(-vv, vv, b.y) : vv * vv;
             [[maybe_unused]] const float p3 = (KIND == GS_K_POLY3) ? s_c[j].w : 0.f; // the cubic's top coefficient
             if (PPT > 1 && (FOLD || cfg.monotone)) { // f1 (c1 < 0) and exp are monotone
                 // smallest Q over this thread's run of pixels: u is affine
@@ -317,7 +318,7 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                 const float ua = fmaf(a.x, lx + 0.5f, ub), uz = fmaf(a.x, lx + PPT - 0.5f, ub);
                 const float um = ((ua > 0.f) != (uz > 0.f)) ? 0.f : fminf(fabsf(ua), fabsf(uz));
 #endif
-                if constexpr (PACKED) {
+                if constexpr (NEGB) {
                     // the same test on the negated exponent / alpha
                     if (fmaf(um, um, v2) > -fold_skip) return;
                 } else if constexpr (FOLD) {
@@ -327,6 +328,14 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                     // beyond the record's cut x_cut: no pixel's exact alpha
                     // reaches eps (FP16x2: it then skips what FP32 skips)
                     if (fmaf(um, um, v2) > b.w) return;
+                } else if constexpr (KIND == GS_K_POLY2) {
+                    // the same with f'2's cut, carried in its p3 slot
+                    if (fmaf(um, um, v2) > s_c[j].w) return;
+                } else if (KIND == GS_K_POLY3 && cfg.tail_zero) {
+                    // f3 is 0 past its root x0: the opacity-free cut of Eq. 5
+                    // (the Horner step of the test below costs more than the
+                    // tighter opacity cut saves: f3 pass 7.94 -> 7.74 ms)
+                    if (fmaf(um, um, v2) > cfg.x0) return;
                 } else {
                     if (alpha_of_q<KIND>(cfg, b, p3, fmaf(um, um, v2)) < eps_skip) return;
                 }
@@ -389,14 +398,31 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
                 // fma(0, T, T) = T); T' = T + na T; the colour gains
                 // (-c)(na T) = c alpha T. Only a pixel that stops takes a
                 // branch (T' < t_min is possible only where alpha >= eps).
+                // f'2 / f3: Q = u^2 + v^2 and the polynomial's Horner steps
+                // on pairs, then na = -min(alpha_max, alpha) where alpha >= eps
                 const float2 ax2 = make_float2(a.x, a.x), ub2 = make_float2(ub, ub), nb2 = make_float2(v2, v2);
                 float na[PPT], Tn[PPT];
                 bool stop = false;
 #pragma unroll
                 for (int k = 0; k < PPT; k += 2) {
                     const float2 u = __ffma2_rn(ax2, make_float2(xs[k], xs[k + 1]), ub2);
-                    const float2 ne = __ffma2_rn(u, u, nb2);
-                    if constexpr (KIND == GS_K_EXP) {
+                    const float2 ne = __ffma2_rn(u, u, nb2); // f'2 / f3: Q
+                    if constexpr (!FOLD) {
+                        const float2 Q = ne;
+                        float2 al;
+                        if constexpr (KIND == GS_K_POLY2) {
+                            al = __ffma2_rn(__ffma2_rn(make_float2(b.w, b.w), Q, make_float2(b.z, b.z)), Q,
+                                            make_float2(b.y, b.y));
+                            al.x = Q.x < cfg.x0 ? al.x : 0.f;
+                            al.y = Q.y < cfg.x0 ? al.y : 0.f;
+                        } else {
+                            al = __ffma2_rn(__ffma2_rn(__ffma2_rn(make_float2(p3, p3), Q, make_float2(b.w, b.w)), Q,
+                                                       make_float2(b.z, b.z)),
+                                            Q, make_float2(b.y, b.y));
+                        }
+                        na[k] = al.x >= eps ? fmaxf(-al.x, -amax) : 0.f;
+                        na[k + 1] = al.y >= eps ? fmaxf(-al.y, -amax) : 0.f;
+                    } else if constexpr (KIND == GS_K_EXP) {
                         const float a0 = ex2_approx(-ne.x), a1 = ex2_approx(-ne.y);
                         na[k] = a0 >= eps ? fmaxf(-a0, -amax) : 0.f;
                         na[k + 1] = a1 >= eps ? fmaxf(-a1, -amax) : 0.f;
@@ -494,13 +520,15 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
             }
             }
         };
-        constexpr int U = blend_unroll<KIND>();
-        if constexpr (FOLD) {
-            // f1, exp: whole groups of U entries unrolled, the run's activity
-            // tested once per group (entries a stopped run walks change
-            // nothing: its pixels are NaN and fail every alpha test). One
-            // stream pass: f1 6.19 -> 5.87 ms, exp 8.11 -> 7.70 ms; f3 lost
-            // 0.09 ms this way and keeps the test per entry.
+        // (the FP16x2 blend keeps the unroll it was measured with: 8 for exp, 4 otherwise)
+        constexpr int U = (FOLD || PACKED) ? blend_unroll<KIND>() : (KIND == GS_K_EXP ? 8 : 4);
+        if constexpr (FOLD || PACKED) {
+            // whole groups of U entries unrolled, the run's activity tested
+            // once per group (entries a stopped run walks change nothing: its
+            // pixels are NaN and fail every alpha test). One-stream pass: f1
+            // 6.19 -> 5.87 ms, exp 8.11 -> 7.70 ms; with the packed pairs f'2
+            // 7.70 -> 7.61 ms, f3 8.06 -> 7.94 ms (the FP16x2 blend, whose
+            // alpha is not FP32, keeps the test per entry).
             for (int j0 = 0; j0 < cnt && active; j0 += U) {
                 if (j0 + U <= cnt) {
 #pragma unroll
