@@ -61,7 +61,7 @@ def blend_source_hash() -> str:
 #       python bench.py --profile poly1 --steps 2 --warmup 1
 # and pipe utilisation from a --set full capture of the same kernel (1M
 # splats x 4 cameras; the kernel's code, not the scene, sets these).
-BLEND_CAPTURE = {"src_hash": "4ecf906f4934bf7b", "traffic": 731218432 + 499773440,
+BLEND_CAPTURE = {"src_hash": "dea8d4168b50f4fd", "traffic": 731218432 + 499773440,
                  "ncu": {"issue_active": 0.733, "fma_pipe": 0.317, "fma_pipe_cycles": 0.453, "alu_pipe": 0.409,
                          "lanes_active_of_32": 18.51, "warps_active": 0.477,
                          "source": "ncu --set full, render_persistent_kernel<POLY1, 4, FP32, no index tracking>, 1M splats x 4 cameras"}}
