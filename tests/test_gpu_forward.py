@@ -324,6 +324,25 @@ def test_tile_shapes_and_pixels_per_thread(gs, orc, small):
         assert worst < TOL_FP32, tile
 
 
+@pytest.mark.parametrize("kind", ["exp", "poly1", "poly2", "poly3"])
+@pytest.mark.parametrize("cull", ["universal", "opacity"])
+def test_packed_pixel_pairs_equal_scalar_update(gs, small, kind, cull):
+    """Two and four pixels per thread update pixel pairs with packed FP32x2
+    FMAs (signs of the colours, and for f1 / exp of beta and the exponent,
+    flipped so that no operand is negated); one pixel per thread takes the
+    scalar update. Every rounding step is the same, so images and final T
+    are equal bit for bit, for every kernel and cut."""
+    from paper_2603_18707_b300 import synth
+    cam = synth.camera_small(100, 75)
+    out = []
+    for p in (1, 2, 4):
+        R = _gpu(gs, small, [cam], kind, cull, px_per_thread=p)
+        out.append((R.images()[0].cpu().numpy(), R.per_camera(R.final_T)[0].cpu().numpy()))
+    for img, T in out[1:]:
+        assert np.array_equal(img, out[0][0])
+        assert np.array_equal(T, out[0][1])
+
+
 @pytest.mark.parametrize("kind,cull", [("poly1", "opacity"), ("exp", "opacity"), ("poly3", "universal")])
 def test_n_eval_matches_oracle_count(gs, orc, small, kind, cull):
     """The per-pixel evaluation count (the numerator of Gsplat-evals/s): the
