@@ -32,6 +32,9 @@ namespace {
 
 constexpr int kMaxBatch = 256;
 // FP32 blend on packed FP32x2 pixel pairs (see render_tile).
+#ifndef GS_BLEND_PAIRS
+#define GS_BLEND_PAIRS 1 // f1 / exp: skip tests of entry pairs on FP32x2 pairs
+#endif
 #ifndef GS_BLEND_PACKED
 #define GS_BLEND_PACKED 1
 #endif
@@ -174,6 +177,10 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
     // needs a negation (the results are bit-identical to the scalar update)
     constexpr bool PACKED = GS_BLEND_PACKED && !HALF && PPT % 2 == 0;
     constexpr bool NEGB = PACKED && FOLD;
+    // f1 / exp packed: entries staged as pairs (2m, 2m + 1), field by field,
+    // so that the skip tests of both run on FP32x2 pairs too: s_a[m] = (ux,
+    // uy) of both, s_a[kMaxBatch / 2 + m] = (u0, vy), s_b[m] = (v0, -p0)
+    constexpr bool PAIRS = GS_BLEND_PAIRS && GS_SKIP_MID && NEGB;
     // f1's alpha never exceeds its entry's p0 = o' c0 (beta - s^2 <= beta <=
     // p0, also as rounded), so a batch whose entries all have p0 <= alpha_max
     // is walked without the clamp (for the paper's f1, c0 = 0.773: always)
@@ -268,14 +275,36 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
             __syncthreads(); // the exchange is read before the batch is staged over it
         }
         bool big = false; // a staged f1 entry with p0 > alpha_max
+        const int cnt = (int)min((uint32_t)B, n - base);
+        if (PAIRS && (cnt & 1) && threadIdx.x == 0) {
+            // an odd count's last pair gets a second entry that every run skips
+            float *q0 = reinterpret_cast<float *>(s_a + (cnt >> 1));
+            float *q1 = reinterpret_cast<float *>(s_a + kMaxBatch / 2 + (cnt >> 1));
+            float *q2 = reinterpret_cast<float *>(s_b + (cnt >> 1));
+            q0[1] = q0[3] = q1[1] = q1[3] = q2[1] = 0.f;
+            q2[3] = INFINITY; // -beta = +inf: the run's bound never reaches eps
+        }
         for (int i = threadIdx.x; i < B; i += nthreads) {
             if (base + i < n) {
                 uint32_t v = g.vals[rg.x + base + i];
                 if (v >= g.n_records) v = 0; // only after a timed-out sort wait
                 const BlendCoef k = make_coef<KIND, FOLD>(cfg, g.rec[3 * (size_t)v + 0],
                                                           g.rec[3 * (size_t)v + 1], g.rec[3 * (size_t)v + 2], ox, oy);
-                s_a[i] = k.a;
-                s_b[i] = k.b;
+                if constexpr (PAIRS) {
+                    const int h = i & 1;
+                    float *q0 = reinterpret_cast<float *>(s_a + (i >> 1));
+                    float *q1 = reinterpret_cast<float *>(s_a + kMaxBatch / 2 + (i >> 1));
+                    float *q2 = reinterpret_cast<float *>(s_b + (i >> 1));
+                    q0[h] = k.a.x;
+                    q0[2 + h] = k.a.y;
+                    q1[h] = k.a.z;
+                    q1[2 + h] = k.a.w;
+                    q2[h] = k.b.x;
+                    q2[2 + h] = -k.b.y;
+                } else {
+                    s_a[i] = k.a;
+                    s_b[i] = k.b;
+                }
                 s_c[i] = PACKED ? make_float4(-k.c.x, -k.c.y, -k.c.z, k.c.w) : k.c;
                 if (NOCLAMP_OK) big |= k.b.y > amax;
                 if (HALF) {
@@ -290,56 +319,12 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
             }
         }
         const int need_clamp = __syncthreads_or(big);
-        const int cnt = (int)min((uint32_t)B, n - base);
         // the walk over the batch, with or without the alpha_max clamp
         auto walk = [&](auto clamp_tag) {
         [[maybe_unused]] constexpr bool CLAMP = decltype(clamp_tag)::value;
-        // one entry of the batch for this thread's run (a return skips it)
-        auto entry = [&](const int j) {
-            const float4 a = s_a[j];
-            const float4 b = s_b[j];
-            const float ub = fmaf(a.y, y, a.z);
-            const float vv = fmaf(a.w, y, b.x);
-            // FOLD: beta (NEGB: -beta, exactly, as fma(-x, y, z) = -fma(x, y, -z))
-            const float v2 = NEGB ? fmaf(vv, vv, -b.y) : FOLD ? fmaf(-vv, vv, b.y) : vv * vv;
-            [[maybe_unused]] const float p3 = (KIND == GS_K_POLY3) ? s_c[j].w : 0.f; // the cubic's top coefficient
-            if (PPT > 1 && (FOLD || cfg.monotone)) { // f1 (c1 < 0) and exp are monotone
-                // smallest Q over this thread's run of pixels: u is affine
-                // along the run with slope ux = a.x > 0, so its smallest |u|
-                // is max(0, |u(run centre)| - half-width * ux) (0 when u
-                // changes sign). With k non-increasing, alpha there bounds
-                // every pixel's; the skip threshold sits below eps so that
-                // rounding can never skip an entry that a pixel would take.
-#if GS_SKIP_MID
-                const float umid = fmaf(a.x, xmid, ub);
-                const float um = fmaxf(fmaf(-0.5f * (PPT - 1), a.x, fabsf(umid)), 0.f);
-#else
-                // the run's ends (not xs[], which is NaN for stopped pixels)
-                const float ua = fmaf(a.x, lx + 0.5f, ub), uz = fmaf(a.x, lx + PPT - 0.5f, ub);
-                const float um = ((ua > 0.f) != (uz > 0.f)) ? 0.f : fminf(fabsf(ua), fabsf(uz));
-#endif
-                if constexpr (NEGB) {
-                    // the same test on the negated exponent / alpha
-                    if (fmaf(um, um, v2) > -fold_skip) return;
-                } else if constexpr (FOLD) {
-                    // the run's largest exponent / alpha is beta - sm^2
-                    if (fmaf(-um, um, v2) < fold_skip) return;
-                } else if constexpr (KIND == GS_K_POLY1 || KIND == GS_K_EXP) {
-                    // beyond the record's cut x_cut: no pixel's exact alpha
-                    // reaches eps (FP16x2: it then skips what FP32 skips)
-                    if (fmaf(um, um, v2) > b.w) return;
-                } else if constexpr (KIND == GS_K_POLY2) {
-                    // the same with f'2's cut, carried in its p3 slot
-                    if (fmaf(um, um, v2) > s_c[j].w) return;
-                } else if (KIND == GS_K_POLY3 && cfg.tail_zero) {
-                    // f3 is 0 past its root x0: the opacity-free cut of Eq. 5
-                    // (the Horner step of the test below costs more than the
-                    // tighter opacity cut saves: f3 pass 7.94 -> 7.74 ms)
-                    if (fmaf(um, um, v2) > cfg.x0) return;
-                } else {
-                    if (alpha_of_q<KIND>(cfg, b, p3, fmaf(um, um, v2)) < eps_skip) return;
-                }
-            }
+        // the update of this thread's run by entry j (reached by its skip test)
+        auto update = [&](const int j, const float4 &a, const float4 &b, const float ub, const float v2,
+                          const float p3) {
             const float4 col = s_c[j];
             [[maybe_unused]] const uint32_t pos = base + j + 1;
             if constexpr (HALF) {
@@ -520,9 +505,88 @@ __device__ __forceinline__ void render_tile(const CamTable &cams, const CfgDev &
             }
             }
         };
+        // one entry of the batch for this thread's run (a return skips it)
+        auto entry = [&](const int j) {
+            const float4 a = s_a[j];
+            const float4 b = s_b[j];
+            const float ub = fmaf(a.y, y, a.z);
+            const float vv = fmaf(a.w, y, b.x);
+            // FOLD: beta (NEGB: -beta, exactly, as fma(-x, y, z) = -fma(x, y, -z))
+            const float v2 = NEGB ? fmaf(vv, vv, -b.y) : FOLD ? fmaf(-vv, vv, b.y) : vv * vv;
+            [[maybe_unused]] const float p3 = (KIND == GS_K_POLY3) ? s_c[j].w : 0.f; // the cubic's top coefficient
+            if (PPT > 1 && (FOLD || cfg.monotone)) { // f1 (c1 < 0) and exp are monotone
+                // smallest Q over this thread's run of pixels: u is affine
+                // along the run with slope ux = a.x > 0, so its smallest |u|
+                // is max(0, |u(run centre)| - half-width * ux) (0 when u
+                // changes sign). With k non-increasing, alpha there bounds
+                // every pixel's; the skip threshold sits below eps so that
+                // rounding can never skip an entry that a pixel would take.
+#if GS_SKIP_MID
+                const float umid = fmaf(a.x, xmid, ub);
+                const float um = fmaxf(fmaf(-0.5f * (PPT - 1), a.x, fabsf(umid)), 0.f);
+#else
+                // the run's ends (not xs[], which is NaN for stopped pixels)
+                const float ua = fmaf(a.x, lx + 0.5f, ub), uz = fmaf(a.x, lx + PPT - 0.5f, ub);
+                const float um = ((ua > 0.f) != (uz > 0.f)) ? 0.f : fminf(fabsf(ua), fabsf(uz));
+#endif
+                if constexpr (NEGB) {
+                    // the same test on the negated exponent / alpha
+                    if (fmaf(um, um, v2) > -fold_skip) return;
+                } else if constexpr (FOLD) {
+                    // the run's largest exponent / alpha is beta - sm^2
+                    if (fmaf(-um, um, v2) < fold_skip) return;
+                } else if constexpr (KIND == GS_K_POLY1 || KIND == GS_K_EXP) {
+                    // beyond the record's cut x_cut: no pixel's exact alpha
+                    // reaches eps (FP16x2: it then skips what FP32 skips)
+                    if (fmaf(um, um, v2) > b.w) return;
+                } else if constexpr (KIND == GS_K_POLY2) {
+                    // the same with f'2's cut, carried in its p3 slot
+                    if (fmaf(um, um, v2) > s_c[j].w) return;
+                } else if (KIND == GS_K_POLY3 && cfg.tail_zero) {
+                    // f3 is 0 past its root x0: the opacity-free cut of Eq. 5
+                    // (the Horner step of the test below costs more than the
+                    // tighter opacity cut saves: f3 pass 7.94 -> 7.74 ms)
+                    if (fmaf(um, um, v2) > cfg.x0) return;
+                } else {
+                    if (alpha_of_q<KIND>(cfg, b, p3, fmaf(um, um, v2)) < eps_skip) return;
+                }
+            }
+            update(j, a, b, ub, v2, p3);
+        };
+        // the entry pair (2m, 2m + 1) of the pair layout (f1, exp packed):
+        // the skip tests of both entries on FP32x2 pairs, with the same
+        // rounding as entry(): max(umid - h ux, -(umid + h ux)) equals
+        // |umid| - h ux as rounded, since the two FMAs differ in sign only
+        [[maybe_unused]] auto pair = [&](const int m) {
+            const float4 P0 = s_a[m], P1 = s_a[kMaxBatch / 2 + m], P2 = s_b[m];
+            const float2 yy = make_float2(y, y), hh = make_float2(0.5f * (PPT - 1), 0.5f * (PPT - 1));
+            const float2 ux = make_float2(P0.x, P0.y);
+            const float2 ub = __ffma2_rn(make_float2(P0.z, P0.w), yy, make_float2(P1.x, P1.y));
+            const float2 vv = __ffma2_rn(make_float2(P1.z, P1.w), yy, make_float2(P2.x, P2.y));
+            const float2 v2 = __ffma2_rn(vv, vv, make_float2(P2.z, P2.w)); // -beta
+            const float2 umid = __ffma2_rn(ux, make_float2(xmid, xmid), ub);
+            const float2 lo = __ffma2_rn(make_float2(-hh.x, -hh.y), ux, umid), hi = __ffma2_rn(hh, ux, umid);
+            const float2 um = make_float2(fmaxf(fmaxf(lo.x, -hi.x), 0.f), fmaxf(fmaxf(lo.y, -hi.y), 0.f));
+            const float2 t = __ffma2_rn(um, um, v2);
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!(t.x > -fold_skip)) update(2 * m, make_float4(ux.x, 0.f, 0.f, 0.f), z, ub.x, v2.x, 0.f);
+            if (!(t.y > -fold_skip)) update(2 * m + 1, make_float4(ux.y, 0.f, 0.f, 0.f), z, ub.y, v2.y, 0.f);
+        };
         // (the FP16x2 blend keeps the unroll it was measured with: 8 for exp, 4 otherwise)
         constexpr int U = (FOLD || PACKED) ? blend_unroll<KIND>() : (KIND == GS_K_EXP ? 8 : 4);
-        if constexpr (FOLD || PACKED) {
+        if constexpr (PAIRS) {
+            // groups of U entries as U / 2 pairs, as below
+            const int np = (cnt + 1) >> 1;
+            constexpr int UP = U / 2;
+            for (int m0 = 0; m0 < np && active; m0 += UP) {
+                if (m0 + UP <= np) {
+#pragma unroll
+                    for (int mm = 0; mm < UP; ++mm) pair(m0 + mm);
+                } else {
+                    for (int m = m0; m < np; ++m) pair(m);
+                }
+            }
+        } else if constexpr (FOLD || PACKED) {
             // whole groups of U entries unrolled, the run's activity tested
             // once per group (entries a stopped run walks change nothing: its
             // pixels are NaN and fail every alpha test). One-stream pass: f1
