@@ -10,11 +10,11 @@
 //   Q = u^2 + v^2,  alpha = min(alpha_max, o' k(Q)),
 //   skip if alpha < eps; stop (without adding) if T (1 - alpha) < t_min;
 //   C += c alpha T; T *= 1 - alpha.
-// Cost per entry and thread: 2 LDS.128 and a skip test on a lower bound of Q
-// over the run; where reached, pixel pairs update with packed FP32x2 FMAs (u,
-// alpha, T, colours; decisions scalar; exp adds one MUFU ex2 per pixel).
-// Entries go in unrolled groups; a block leaves a list once every pixel has
-// stopped (__syncthreads_count per batch). Bound by FP32 / ALU issue.
+// Cost per entry and thread: 2 LDS.128 (f1, exp: 3 per entry pair, tested as
+// a pair) and a skip test on a lower bound of Q over the run; where reached,
+// pixel pairs update with packed FP32x2 FMAs (decisions scalar; exp adds one
+// MUFU ex2 per pixel). Entries go in unrolled groups; a block leaves a list
+// once every pixel has stopped. Bound by FP32 / ALU instruction issue.
 //
 // Launch modes: one CTA per tile (grid = all tiles of all cameras), or
 // persistent: a grid sized to fill every SM once, each CTA taking the next
